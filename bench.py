@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of randomized blocked QR with column pivoting on one GB300 per rank.
+
+One step = one full factorization A P = Q R (every step of the method: Gaussian
+draw, sketch, per-block pivots, swaps, panel QR, T, trailing update, sketch
+downdate, last block) of an m x n FP64 matrix with singular values
+exp(-i/800), m = n = 16384, b = 128, p = 8, through the C ABI. A is restored
+from a resident copy before every step, outside the timed interval; every
+step touches 2 GiB, far more than the 129 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (each
+rank factors its own matrix): value = all ranks' flops / max rank time.
+`--impl reference` times the CPU oracle instead, on a bounded sample (the
+first blocks of the same factorization).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GFLOP/s & roofline fraction of randomized QRCP at n=16384 vs FP64 GPU, fixed residual"
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # GB300 dense nominal FP64 / bf16 ratio
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--b", type=int, default=128)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
+    ap.add_argument("--seed", type=int, default=1505)
+    ap.add_argument("--cpu-blocks", type=int, default=2, help="blocks of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: str):
+        self.proc = None
+        self.dev = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.dev], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def device_index_for_smi(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def apply_q(F, T, b, X, transpose=False):
+    """Q X or Q^T X from the block reflectors (verification only)."""
+    import torch
+
+    from paper_1505_08115_gb300.flops import block_starts
+
+    m, n = F.shape
+    starts = block_starts(n, b)
+    X = X.clone()
+    for k0 in (starts if transpose else list(reversed(starts))):
+        kb = min(b, n - k0)
+        V = torch.tril(F[k0:, k0:k0 + kb], -1)
+        V[torch.arange(kb), torch.arange(kb)] = 1.0
+        Tk = T[:kb, k0:k0 + kb]
+        W = (Tk.T if transpose else Tk) @ (V.T @ X[k0:])
+        X[k0:] -= V @ W
+    return X
+
+
+def make_matrix(n, seed, device):
+    import numpy as np
+
+    from paper_1505_08115_gb300 import inputs
+
+    return inputs.torch_svd_matrix(n, n, inputs.spectrum_exp(n, 800.0), seed, device=device)
+
+
+def workload_config(a):
+    return {"workload": f"rqrcp m=n={a.n} b={a.b} p={a.p} sketch={a.sketch}, A = U diag(exp(-i/800)) V^T",
+            "m": a.n, "n": a.n, "b": a.b, "p": a.p, "sketch": a.sketch, "precision": "fp64",
+            "l2": "inputs larger than L2 (2 GiB matrix restored before every step)", "parallelism": "replicas"}
+
+
+def cpu_baseline(A0_host, G_host, a, blocks):
+    """Times the CPU oracle on the first `blocks` blocks of the same factorization."""
+    import oracle
+    from paper_1505_08115_gb300.flops import rqrcp_flops
+
+    oracle.build()
+    t0 = time.perf_counter()
+    F, T, perm, done = oracle.rqrcp(A0_host, a.b, a.p, G_host, max_blocks=blocks)
+    dt = time.perf_counter() - t0
+    fl = rqrcp_flops(a.n, a.n, a.b, a.p, max_blocks=blocks)["total"]
+    cores = len(os.sched_getaffinity(0))
+    return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle", "sample": f"first {blocks} blocks ({done} columns) of the same {a.n}x{a.n} "
+                                         f"factorization incl. the initial sketch, {dt:.1f} s"}, dt
+
+
+def run_reference(a, rank):
+    """Reference arm: the CPU oracle as it stands, bounded samples of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    from paper_1505_08115_gb300 import inputs
+    from paper_1505_08115_gb300.flops import rqrcp_flops
+
+    import oracle
+
+    oracle.build()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    if dev == "cuda":
+        A0 = np.asfortranarray(make_matrix(a.n, a.seed, dev).cpu().numpy())
+    else:
+        A0 = inputs.svd_matrix(a.seed, a.n, a.n, inputs.spectrum_exp(a.n, 800.0))
+    G = inputs.sketch_gaussian(a.seed + 1, a.b + a.p, a.n)
+    blocks = 1
+    fl = rqrcp_flops(a.n, a.n, a.b, a.p, max_blocks=blocks)["total"]
+    times = []
+    for s in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        oracle.rqrcp(A0, a.b, a.p, G, max_blocks=blocks)
+        dt = time.perf_counter() - t0
+        if s >= a.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    val = fl / (ms / 1e3) / 1e9
+    cores = len(os.sched_getaffinity(0))
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+           "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                            "sample": f"first {blocks} block of the {a.n}x{a.n} factorization per step"},
+           "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if a.impl == "reference":
+        run_reference(a, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+
+    from paper_1505_08115_gb300 import rqr
+    from paper_1505_08115_gb300.flops import conventional_qr_flops, rqrcp_flops
+
+    rqr.load()  # fails loudly when the CUDA library is missing
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n, b, p = a.n, a.b, a.p
+    sk = rqr.SKETCH_DOWNDATE if a.sketch == "downdate" else rqr.SKETCH_RESAMPLE
+    A0 = make_matrix(n, a.seed + rank, dev)
+    A = rqr.empty_colmajor(n, n, torch.float64, dev)
+    T = rqr.empty_colmajor(b, n, torch.float64, dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64, sk), dtype=torch.uint8, device=dev)
+    seed = a.seed + 1 + rank
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False)
+
+    for _ in range(a.warmup):
+        A.copy_(A0)
+        step()
+    torch.cuda.synchronize()
+    # accuracy of the last warm-up result (random probes; the CPU cannot form Q at this size)
+    T_, perm_, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work)
+    g = torch.Generator(device=dev).manual_seed(7)
+    X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
+    R = torch.triu(A)
+    APx = A0[:, perm.long()] @ X
+    res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
+    orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
+            / torch.linalg.norm(X)).item()
+    del R, APx
+
+    clocks = Clocks(device_index_for_smi(local_rank))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    rqr.profile_enable(True)
+    evs = []
+    for _ in range(a.steps):
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    prof = rqr.profile_read()
+    rqr.profile_enable(False)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    fl = rqrcp_flops(n, n, b, p, resample=(sk == rqr.SKETCH_RESAMPLE))
+    value = world * fl["total"] / (ms / 1e3) / 1e9
+    launches = sum(v["launches"] for v in prof.values())
+
+    # roofline of the dominant kernel: the FP64 DMMA GEMMs of the trailing update
+    pk, src = peaks()
+    peak64 = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+    up = prof["update"]
+    achieved = up["flops"] / (up["ms"] / 1e3) / 1e12 if up["ms"] > 0 else 0.0
+    roof = {"kernel": "trailing update (k_dgemm, mma.sync.m8n8k4.f64)", "bound": "tensor",
+            "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
+            "peak_source": f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 ratio 1.25/2250",
+            "traffic": None}
+
+    out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+           "effective_gflops": world * conventional_qr_flops(n, n) / (ms / 1e3) / 1e9,
+           "residual": res, "orthogonality": orth, "device_status": info,
+           "phases": {k: {"ms": v["ms"] / a.steps, "gflops": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0,
+                          "launches": v["launches"] // a.steps} for k, v in prof.items()},
+           "roofline": roof, "gpu_launches": launches, "clocks": ck}
+
+    if not a.no_e2e:
+        # end to end through the same C-ABI call with host buffers: pinned H2D of A,
+        # factorization, D2H of R/V, T and perm, all inside the timed interval
+        Ah = A0.cpu().pin_memory()
+        Fh = torch.empty_like(Ah).pin_memory()
+        Th = torch.empty((n, b), dtype=torch.float64).pin_memory()
+        Ph = torch.empty(n, dtype=torch.int32).pin_memory()
+        Ad = A  # column-major device buffer
+        e2e_ms = []
+        for it in range(2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Ad.copy_(Ah, non_blocking=True)
+            step()
+            Fh.copy_(Ad, non_blocking=True)
+            Th.copy_(T.mT, non_blocking=True)
+            Ph.copy_(perm, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        em = min(e2e_ms)
+        out["e2e"] = {"value": world * fl["total"] / (em / 1e3) / 1e9, "unit": "GFLOP/s",
+                      "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n + 8 * b * n + 4 * n}
+        del Ah, Fh
+
+    if rank == 0 and not a.no_cpu_baseline:
+        from paper_1505_08115_gb300 import inputs
+
+        Ah = np.asfortranarray(A0.cpu().numpy())
+        # the device draws its own G from the seed; the oracle sample gets a
+        # Gaussian of the same shape from the seeded host generator
+        G = inputs.sketch_gaussian(seed, b + p, n)
+        out["cpu_baseline"], _ = cpu_baseline(Ah, G, a, a.cpu_blocks)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

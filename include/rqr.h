@@ -1,0 +1,152 @@
+/*
+ * rqr.h -- C ABI of the GB300 (sm_103a) library for randomized blocked QR
+ * factorizations (Martinsson, "Blocked rank-revealing QR factorizations: how
+ * randomized sampling can be used to avoid single-vector pivoting", 2015).
+ *
+ * Storage conventions for every entry point:
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *    Element (i, j) of A sits at A[i + j*lda]; indices are 0-based.
+ *  - Pointers marked (device) must point to memory of the GPU that is current
+ *    when the handle was created; (host) pointers are ordinary host memory.
+ *  - The caller owns every buffer. A factor call allocates nothing: scratch
+ *    comes from the caller's workspace (size from rqr_workspace_bytes).
+ *  - Householder vectors are stored below the diagonal of the factored matrix
+ *    with an implicit unit first entry; the orthonormal factor of one block is
+ *    Q_i = I - V_i T_i V_i^T with T_i upper triangular (compact WY, Sec. 5.1).
+ *  - perm[k] is the original column that ends up at position k of A*P.
+ *  - All work is queued on the handle's stream. When `info` is non-NULL the
+ *    call waits for the stream and writes the device status word to *info
+ *    (0 = ok); with info == NULL the call returns as soon as the work is queued.
+ *
+ * Return values: 0 on success; -i when argument i (1-based, as listed) is
+ * invalid (LAPACK convention; nothing is queued); a positive RQR_ERR_* code on
+ * a runtime failure. No C++ exception crosses this interface.
+ */
+#ifndef RQR_H
+#define RQR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rqr_handle_s* rqr_handle_t;
+
+/* Arithmetic of the factorization (the `prec` argument). */
+#define RQR_FP64 0 /* every step in FP64 (A, T are double) */
+#define RQR_FP32 1 /* every step in FP32 (A, T are float) */
+
+/* How the sketch follows the factorization from block to block (`sketch`). */
+#define RQR_SKETCH_DOWNDATE 0 /* draw G once, update Y = G X after each block */
+#define RQR_SKETCH_RESAMPLE 1 /* draw a fresh G_i for every block (Fig. blockQR) */
+
+/* Runtime status codes (positive return values / *info). */
+#define RQR_OK 0
+#define RQR_ERR_CUDA 1        /* a CUDA call failed; the handle stays usable   */
+#define RQR_ERR_NONFINITE 2   /* a NaN/Inf reached a panel norm               */
+#define RQR_ERR_WORKSPACE 4   /* lwork smaller than rqr_workspace_bytes        */
+#define RQR_ERR_UNSUPPORTED 5 /* a combination this build does not implement  */
+#define RQR_ERR_HANDLE 6      /* NULL or destroyed handle                      */
+
+/* Creates a handle bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = legacy default stream). (host) h receives the handle.
+ * The handle owns only a few bytes of device memory for its status word. */
+int rqr_create(rqr_handle_t* h, void* stream);
+
+/* Destroys the handle after waiting for its stream. */
+int rqr_destroy(rqr_handle_t h);
+
+/* Rebinds the handle to another stream (cudaStream_t). */
+int rqr_set_stream(rqr_handle_t h, void* stream);
+
+/* Bytes of device workspace that rqrcp_factor (q < 0) or rurv_factor (q >= 0)
+ * needs for the given shape, block size b, over-sampling p and precision.
+ * (host) bytes receives the size. */
+int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch, size_t* bytes);
+
+/* Randomized blocked QR with column pivoting, A P = Q R (Sec. 4.1, 4.3, 5.1, 5.2;
+ * Method 1 of Sec. 7 with over-sampling p).
+ *   m, n     rows and columns, m >= n >= 0.
+ *   A        (device, in/out) m x n, ld lda. On exit R is in the upper triangle
+ *            and the Householder vectors of every block below the diagonal.
+ *   b        block size, 1 <= b; p >= 0 over-sampling; the sketch has l = b + p rows.
+ *   seed     Philox4x32-10 key for the Gaussian sketch when G == NULL.
+ *   G        (device, optional) the Gaussian: DOWNDATE: l x m, ld ldg.
+ *            RESAMPLE: the blocks G_i (l x (m - k0)), ld l, one after another,
+ *            for every block that is not the last. NULL: drawn from `seed`
+ *            (stream = block index for RESAMPLE, 0 for DOWNDATE).
+ *   T        (device, out) b x n, ld ldt >= b: the block starting at column k0
+ *            stores its upper-triangular T at T(0:b_i, k0:k0+b_i).
+ *   perm     (device, out) n int32.
+ *   prec     RQR_FP64 or RQR_FP32 (then A, G, T are float).
+ *   sketch   RQR_SKETCH_DOWNDATE or RQR_SKETCH_RESAMPLE.
+ *   work     (device) workspace of lwork bytes, 256-byte aligned.
+ *   info     (host, optional) see the header comment.
+ * The last block (n - k0 <= b) is finished by classical pivoted QR (Fig. QR). */
+int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, uint64_t seed,
+                 const void* G, int ldg, void* T, int ldt, int32_t* perm, int prec, int sketch,
+                 void* work, size_t lwork, int* info);
+
+/* Blocked QR with orthonormal pivoting A P = Q R, P = S_0 S_1 ... (Sec. 4.2,
+ * 6.3, 6.4 without the diagonalisation of the diagonal blocks; Method 2 of Sec. 7,
+ * and the power scheme of Method 3).
+ *   A        (device, in/out) m x n, ld lda: R above, left reflectors below.
+ *   b, p, q  block size, over-sampling (l = b + p), power steps q >= 0.
+ *   k        stop once k0 >= k (truncated rank-k URV); k <= 0 or k >= n: full.
+ *   seed, G  Gaussian blocks G_i (l x (m - k0), ld l, one after another,
+ *            one per block including the last), or NULL to draw from seed.
+ *   TU       (device, out) b x n, ld ldtu: T of the left reflectors per block.
+ *   WV       (device, out) n x n, ld ldwv: block i keeps the Householder vectors
+ *            of S_i below the diagonal of WV(k0:n, k0:k0+b_i).
+ *   TV       (device, out) b x n, ld ldtv: T of S_i per block.
+ *   prec     RQR_FP64. */
+int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k,
+                uint64_t seed, const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV,
+                int ldtv, int prec, void* work, size_t lwork, int* info);
+
+/* Forms the first `ncols` columns of Q = Q_0 Q_1 ... from the block reflectors
+ * that a factor call left in F (m x n, ld ldf) and T (b x n, ld ldt).
+ * Q (device, out) m x ncols, ld ldq; prec RQR_FP64 or RQR_FP32. */
+int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt,
+               void* Q, int ldq, int ncols, int prec, void* work, size_t lwork);
+
+/* Fills out[0:count] (device) with N(0,1) samples: element e is lane e%4 of
+ * Philox4x32-10 block e/4 with counter {lo(e/4), hi(e/4), lo(stream),
+ * hi(stream)} and key {lo(seed), hi(seed)}, through Box-Muller on the pairs
+ * (lane0, lane1), (lane2, lane3) with u = (x + 0.5) 2^-32. prec selects
+ * double (RQR_FP64) or float (RQR_FP32) output. */
+int rqr_gauss_fill(rqr_handle_t h, uint64_t seed, uint64_t stream, int64_t count, void* out, int prec);
+
+/* Raw Philox4x32-10 blocks: out[4*i + t] = lane t of the block with counter
+ * {ctr0 + i, 0, ctr2, ctr3} (device out, count blocks). */
+int rqr_philox_raw(rqr_handle_t h, uint32_t ctr0, uint32_t ctr2, uint32_t ctr3, uint32_t key0,
+                   uint32_t key1, int64_t count, uint32_t* out);
+
+/* Tracing: steps of the method timed with CUDA events on the handle's stream.
+ * Phase indices for rqr_profile_read (paper section in brackets): */
+#define RQR_PHASE_SKETCH 0   /* Gaussian draw and Y = G A [Sec. 4.1]            */
+#define RQR_PHASE_PIVOT 1    /* b steps of Fig. QR on the sketch [Sec. 4.1, 4.3] */
+#define RQR_PHASE_SWAP 2     /* column swaps of A, Y, perm [Fig. blockQR]        */
+#define RQR_PHASE_PANEL 3    /* panel Householder QR and T [Sec. 3.2, 5.1]       */
+#define RQR_PHASE_UPDATE 4   /* trailing update (I - V T V^T)^T A22 [Fig. blockQR] */
+#define RQR_PHASE_DOWNDATE 5 /* sketch downdate (not in the paper)               */
+#define RQR_PHASE_FINAL 6    /* last block by Fig. QR [Fig. blockQR, last step]  */
+#define RQR_NUM_PHASES 7
+
+/* Turns per-phase event recording on (on != 0) or off and clears the counters. */
+int rqr_profile_enable(rqr_handle_t h, int on);
+
+/* Waits for the handle's stream, then writes per phase (host arrays of nphase
+ * entries, any may be NULL): ms = summed event time, flops = algorithmic flop
+ * count of the work queued in that phase, launches = kernels launched in it
+ * (counted whether or not recording is on). Clears the counters. */
+int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches, int nphase);
+
+/* Library version string (static storage). */
+const char* rqr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

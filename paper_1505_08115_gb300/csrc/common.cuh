@@ -1,0 +1,144 @@
+// common.cuh -- shared helpers for the sm_103a kernels of the randomized
+// blocked QR library: launch checks, warp reductions, the workspace carver and
+// the GEMM entry used by every dense contraction of the method.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/rqr.h"
+
+namespace rqr {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time too)
+
+struct Ctx {
+  cudaStream_t stream;
+  int sms;             // multiprocessor count of the device
+  int* status;         // device status word (RQR_ERR_* or 0)
+  int64_t* nlaunch;    // host-side count of kernel launches (may be null)
+};
+
+// Counts kernel launches issued through a context (tracing aid).
+inline void note_launch(const Ctx& c, int64_t n = 1) {
+  if (c.nlaunch) *c.nlaunch += n;
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sign with sign(0) = +1 (reflector convention, Sec. 3.1).
+template <typename T>
+__device__ __forceinline__ T sgn0(T x) { return x < T(0) ? T(-1) : T(1); }
+
+// ---------------------------------------------------------------- workspace
+// Bump allocator over the caller's workspace; every carve is 256-byte aligned.
+struct Carver {
+  char* base;
+  size_t cap, used;
+  bool dry;  // size query only
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+  bool ok() const { return dry || used <= cap; }
+};
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- GEMM
+// C = alpha * op(A) * op(B) + beta * C, column-major, M x N result, inner K.
+// op(A) = A (ta = false, A is M x K) or A^T (ta = true, A is K x M); same for B.
+// `part` is scratch for split-K partial sums (capacity part_cap elements);
+// the contraction runs in the precision of T (FP64 on the DMMA pipe, FP32 on
+// the FFMA pipe).
+template <typename T>
+void gemm(const Ctx& c, bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, const T* B,
+          int ldb, T beta, T* C, int ldc, T* part, size_t part_cap);
+
+// Split-K partial-buffer elements that gemm() may use for this shape.
+size_t gemm_part_elems(int M, int N, int K, int sms);
+
+// ---------------------------------------------------------------- kernels
+// Gaussian fill (rng.cu)
+template <typename T>
+void gauss_fill(const Ctx& c, uint64_t seed, uint64_t stream, int64_t count, T* out);
+// 2-D fill of an r x cols column-major block (ld) from the stream; element
+// (i, j) takes stream index i + j*r.
+template <typename T>
+void gauss_fill_2d(const Ctx& c, uint64_t seed, uint64_t stream, int r, int cols, T* out, int ld);
+
+void philox_raw(const Ctx& c, uint32_t ctr0, uint32_t ctr2, uint32_t ctr3, uint32_t k0, uint32_t k1,
+                int64_t count, uint32_t* out);
+
+// Matrix copy / fill helpers (util in panel.cu)
+template <typename T>
+void copy_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
+template <typename T>
+void set_mat(const Ctx& c, int r, int cols, T val, T* dst, int ldd);
+
+// Explicit unit-lower-trapezoidal V (m' x kb, ld ldv) from the factored panel.
+template <typename T>
+void make_vx(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv);
+
+// ---------------------------------------------------------------- panel QR
+struct PanelWork;
+template <typename T>
+struct PanelBufs {
+  T* part;      // [2][C][nc + 1] partial sums (ping-pong)
+  T* rowbuf;    // [2][nc] published row values (ping-pong)
+  T* tau;       // [nc]
+  int* ipart;   // unused placeholder for alignment
+  int C;        // number of CTAs
+  int rows;     // rows per CTA
+};
+
+template <typename T>
+size_t panel_scratch_elems(int mp, int nc, int sms);
+
+// Unpivoted Householder QR of the mp x nc panel P (ld ldp), Sec. 3.2.
+// tau receives nc scaling factors (0 where no reflector).
+template <typename T>
+void panel_qr(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch);
+
+// Classical pivoted QR (Fig. QR) of rows r0..m-1, columns c0..c0+nc-1 of the
+// m x * matrix A; swaps move all m rows and perm[c0..].
+template <typename T>
+void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int32_t* perm, T* tau,
+                T* scratch);
+
+// T factor from the Gram matrix of V (kb x kb, ld ldg) and tau (Sec. 5.1).
+template <typename T>
+void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt);
+
+// ---------------------------------------------------------------- sketch pivots
+template <typename T>
+size_t ypick_scratch_elems(int l, int np, int b, int sms);
+
+// First bsteps steps of Fig. QR on the l x np sketch Y (read only); writes the
+// picked positions (sequential-swap semantics) to picks[bsteps].
+template <typename T>
+void ypick(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy, int* picks, T* scratch);
+
+// Applies the swaps (j, picks[j]), j = 0..kb-1, in order to columns k0.. of
+// A (all m rows), to columns y0.. of Y (l rows, optional) and to perm[k0..].
+template <typename T>
+void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy,
+                 int y0, int32_t* perm, T* tmp, int* imap);
+
+}  // namespace rqr
+
+#define RQR_CUDA_TRY(x)                                  \
+  do {                                                   \
+    cudaError_t e_ = (x);                                \
+    if (e_ != cudaSuccess) return RQR_ERR_CUDA;          \
+  } while (0)

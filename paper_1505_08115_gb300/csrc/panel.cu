@@ -1,0 +1,557 @@
+// panel.cu -- Householder QR of a tall panel (Sec. 3.2), classical pivoted QR
+// of the last block (Fig. QR, Sec. 3.3), and the compact-WY T factor
+// (Sec. 5.1, WY remark).
+//
+// A panel of mp x nc (mp up to ~16k, nc = b <= 512) is spread over C CTAs,
+// each owning a contiguous slice of rows. One launch handles one column j:
+//   * every CTA reads the reflector coefficients of column j (tau, beta,
+//     d = alpha - beta and w_c = tau * v^T x_c for c > j) prepared by the
+//     previous launch, writes v = x_j/d over its rows, applies
+//     x_c <- x_c - w_c v to its rows, and in the same pass accumulates its
+//     partial sums for column j+1 (||x_{j+1}||^2 below the diagonal and
+//     x_{j+1}^T x_c), which need only the freshly updated values;
+//   * the owner of row j+1 publishes that row;
+//   * the last CTA to finish (atomic ticket after a fence, no waiting) adds
+//     the partials in CTA order and prepares the coefficients of column j+1.
+// The identity v^T x_c = x_c(j) + (sum_{i>j} x_j(i) x_c(i)) / d lets one
+// reduction per column serve both the norm and every dot product.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rqr {
+
+namespace {
+
+constexpr int PT = 256;        // threads per panel CTA
+constexpr int NCOEF = 4;       // tau, beta, d, has-reflector
+
+struct PanelArgs {
+  int mp, nc, R, ldp;
+};
+
+// Coefficients of the reflector of column j from its squared norm below the
+// diagonal (s_below) and its diagonal entry alpha (Sec. 3.1 with sign(0)=+1).
+template <typename T>
+__device__ void reflector_coef(int j, int mp, T alpha, T s_below, T* coef, T* tau_out, int* status) {
+  T tau = T(0), beta = alpha, d = T(1), has = T(0);
+  if (mp - j >= 2) {
+    has = T(1);
+    const T s = alpha * alpha + s_below;
+    if (!isfinite(s)) atomicCAS(status, 0, RQR_ERR_NONFINITE);
+    if (s == T(0)) {
+      beta = T(0);
+    } else {
+      const T nrm = sqrt(s);
+      beta = -sgn0(alpha) * nrm;
+      d = alpha - beta;
+      tau = (beta - alpha) / beta;
+    }
+  }
+  coef[0] = tau;
+  coef[1] = beta;
+  coef[2] = d;
+  coef[3] = has;
+  tau_out[j] = tau;
+}
+
+// Last-CTA step: totals of the partials for column jn (entry 0 = squared norm
+// below the diagonal, entry 1 + c = dot with column c) and its coefficients.
+template <typename T>
+__device__ void finish_coef(int jn, const PanelArgs& a, const T* part, const T* rowbuf, T* coef, T* tau_out,
+                            int* status, T* red) {
+  const int C = gridDim.x, tid = threadIdx.x, nc = a.nc;
+  for (int c = jn + tid; c < nc; c += PT) {
+    const int e = (c == jn) ? 0 : 1 + c;
+    T s = T(0);
+    for (int q = 0; q < C; ++q) s += __ldcg(part + (size_t)q * (nc + 1) + e);
+    red[c] = s;
+  }
+  __syncthreads();
+  if (tid == 0) reflector_coef<T>(jn, a.mp, __ldcg(rowbuf + jn), red[jn], coef, tau_out, status);
+  __syncthreads();
+  const T tau = coef[0], d = coef[2];
+  for (int c = jn + 1 + tid; c < nc; c += PT)
+    coef[NCOEF + c] = tau == T(0) ? T(0) : tau * (__ldcg(rowbuf + c) + red[c] / d);
+}
+
+// Ticket: returns true in exactly one CTA, the last one to get here, after all
+// other CTAs' global writes are visible to it.
+__device__ bool last_cta(int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(counter, 1);
+    last = (t == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < PT / 32; ++i) s += sh[i];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// ------------------------------------------------------------ unpivoted panel
+template <typename T>
+__global__ void __launch_bounds__(PT) k_panel_init(PanelArgs a, const T* __restrict__ P, T* part, T* rowbuf,
+                                                   T* coef, T* tau, int* counter, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);
+  __shared__ T wsum[PT / 32];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  T* myp = part + (size_t)q * (a.nc + 1);
+  // norm of column 0 below the diagonal
+  T s = T(0);
+  for (int rr = tid; rr < nr; rr += PT) {
+    const int i = r0 + rr;
+    if (i > 0) {
+      const T x = P[i];
+      s += x * x;
+    }
+  }
+  s = block_sum(s, wsum);
+  if (tid == 0) myp[0] = s;
+  for (int c = 1 + warp; c < a.nc; c += PT / 32) {
+    T acc = T(0);
+    for (int rr = lane; rr < nr; rr += 32) {
+      const int i = r0 + rr;
+      if (i > 0) acc += P[i] * P[i + (size_t)c * a.ldp];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) myp[1 + c] = acc;
+  }
+  if (r0 == 0 && nr > 0)
+    for (int c = tid; c < a.nc; c += PT) rowbuf[c] = P[(size_t)c * a.ldp];
+  if (last_cta(counter)) {
+    finish_coef<T>(0, a, part, rowbuf, coef, tau, status, red);
+    if (tid == 0) *counter = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PT) k_panel_step(int j, PanelArgs a, T* __restrict__ P, const T* coef_in,
+                                                   T* coef_out, T* part, T* rowbuf_out, T* tau, int* counter,
+                                                   int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* w = reinterpret_cast<T*>(smem_raw);      // [nc]
+  T* vs = w + a.nc;                           // [R]
+  T* xn = vs + a.R;                           // [R]
+  __shared__ T wsum[PT / 32];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = a.nc, ldp = a.ldp;
+  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  for (int c = tid; c < nc; c += PT) w[c] = c > j ? coef_in[NCOEF + c] : T(0);
+  const T tauj = coef_in[0], beta = coef_in[1], d = coef_in[2];
+  const bool has = coef_in[3] != T(0);
+  __syncthreads();
+  T* Pj = P + (size_t)j * ldp;
+  T* Pj1 = P + (size_t)(j + 1) * ldp;
+  const bool next = j + 1 < nc;
+  // column j -> v (rows > j); column j+1 updated (rows > j); row j finished
+  for (int rr = tid; rr < nr; rr += PT) {
+    const int i = r0 + rr;
+    if (i > j) {
+      T v = Pj[i];
+      if (has) v = tauj == T(0) ? T(0) : v / d;
+      Pj[i] = v;
+      vs[rr] = v;
+      if (next) {
+        const T x = Pj1[i] - w[j + 1] * v;
+        Pj1[i] = x;
+        xn[rr] = x;
+        if (i == j + 1) rowbuf_out[j + 1] = x;
+      }
+    } else if (i == j) {
+      if (has) Pj[j] = beta;
+      for (int c = j + 1; c < nc; ++c) P[j + (size_t)c * ldp] -= w[c];
+    }
+  }
+  __syncthreads();
+  if (next) {
+    T* myp = part + (size_t)q * (nc + 1);
+    T s = T(0);
+    for (int rr = tid; rr < nr; rr += PT)
+      if (r0 + rr > j + 1) s += xn[rr] * xn[rr];
+    s = block_sum(s, wsum);
+    if (tid == 0) myp[0] = s;
+    for (int c = j + 2 + warp; c < nc; c += PT / 32) {
+      T* Pc = P + (size_t)c * ldp;
+      const T wc = w[c];
+      T acc = T(0);
+      for (int rr = lane; rr < nr; rr += 32) {
+        const int i = r0 + rr;
+        if (i > j) {
+          const T x = Pc[i] - wc * vs[rr];
+          Pc[i] = x;
+          if (i > j + 1) acc += xn[rr] * x;
+          else rowbuf_out[c] = x;
+        }
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) myp[1 + c] = acc;
+    }
+    if (last_cta(counter)) {
+      finish_coef<T>(j + 1, a, part, rowbuf_out, coef_out, tau, status, w);
+      if (tid == 0) *counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------ pivoted block
+// Norms of all columns c >= jn over rows >= jn (partials), then the last CTA
+// picks the largest (lowest position on ties) into piv[jn].
+template <typename T>
+__device__ void norms_and_pick(int jn, int nsteps, const PanelArgs& a, const T* P, T* part, int* piv, int* counter,
+                               T* red) {
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  T* myp = part + (size_t)q * (a.nc + 1);
+  for (int c = jn + warp; c < a.nc; c += PT / 32) {
+    const T* Pc = P + (size_t)c * a.ldp;
+    T acc = T(0);
+    for (int rr = lane; rr < nr; rr += 32) {
+      const int i = r0 + rr;
+      if (i >= jn) acc += Pc[i] * Pc[i];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) myp[1 + c] = acc;
+  }
+  if (last_cta(counter)) {
+    for (int c = jn + tid; c < a.nc; c += PT) {
+      T s = T(0);
+      for (int qq = 0; qq < (int)gridDim.x; ++qq) s += __ldcg(part + (size_t)qq * (a.nc + 1) + 1 + c);
+      red[c] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int best = jn;
+      T bn = T(-1);
+      for (int c = jn; c < a.nc; ++c)
+        if (red[c] > bn) { bn = red[c]; best = c; }
+      piv[jn] = best;
+      *counter = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PT) k_qrcp_init(PanelArgs a, const T* P, T* part, int* piv, int* counter) {
+  extern __shared__ unsigned char smem_raw[];
+  norms_and_pick<T>(0, 0, a, P, part, piv, counter, reinterpret_cast<T*>(smem_raw));
+}
+
+// Swap column j with piv[j] over all m rows of A (the block starts at row and
+// column k0 of A), swap perm, then partials of column j and coefficients.
+template <typename T>
+__global__ void __launch_bounds__(PT) k_qrcp_pick(int j, PanelArgs a, int k0, int m, T* A, int lda, int32_t* perm,
+                                                  const int* piv, T* part, T* rowbuf, T* coef, T* tau, int* counter,
+                                                  int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);
+  __shared__ T wsum[PT / 32];
+  const int q = blockIdx.x, C = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = a.nc;
+  const int cs = piv[j];
+  T* P = A + k0 + (size_t)k0 * lda;  // block origin; ldp == lda
+  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  if (cs != j) {
+    T* x = A + (size_t)(k0 + j) * lda;
+    T* y = A + (size_t)(k0 + cs) * lda;
+    for (int rr = tid; rr < nr; rr += PT) {
+      const int i = k0 + r0 + rr;
+      const T t = x[i];
+      x[i] = y[i];
+      y[i] = t;
+    }
+    const int Rt = (k0 + C - 1) / C;  // rows above the block
+    const int t0 = q * Rt, t1 = min(k0, t0 + Rt);
+    for (int i = t0 + tid; i < t1; i += PT) {
+      const T t = x[i];
+      x[i] = y[i];
+      y[i] = t;
+    }
+    if (q == 0 && tid == 0) {
+      const int32_t t = perm[k0 + j];
+      perm[k0 + j] = perm[k0 + cs];
+      perm[k0 + cs] = t;
+    }
+  }
+  __syncthreads();
+  const T* Pj = P + (size_t)j * lda;
+  T* myp = part + (size_t)q * (nc + 1);
+  T s = T(0);
+  for (int rr = tid; rr < nr; rr += PT) {
+    const int i = r0 + rr;
+    if (i > j) s += Pj[i] * Pj[i];
+  }
+  s = block_sum(s, wsum);
+  if (tid == 0) myp[0] = s;
+  for (int c = j + 1 + warp; c < nc; c += PT / 32) {
+    const T* Pc = P + (size_t)c * lda;
+    T acc = T(0);
+    for (int rr = lane; rr < nr; rr += 32) {
+      const int i = r0 + rr;
+      if (i > j) acc += Pj[i] * Pc[i];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) myp[1 + c] = acc;
+  }
+  if (j >= r0 && j < r1)
+    for (int c = j + tid; c < nc; c += PT) rowbuf[c] = P[j + (size_t)c * lda];
+  if (last_cta(counter)) {
+    finish_coef<T>(j, a, part, rowbuf, coef, tau, status, red);
+    if (tid == 0) *counter = 0;
+  }
+}
+
+// Apply the coefficients of column j to every later column; then partial norms
+// for the next pick.
+template <typename T>
+__global__ void __launch_bounds__(PT) k_qrcp_apply(int j, int nsteps, PanelArgs a, T* P, const T* coef, T* part,
+                                                   int* piv, int* counter) {
+  extern __shared__ unsigned char smem_raw[];
+  T* w = reinterpret_cast<T*>(smem_raw);  // [nc]
+  T* vs = w + a.nc;                       // [R]
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = a.nc, ldp = a.ldp;
+  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  for (int c = tid; c < nc; c += PT) w[c] = c > j ? coef[NCOEF + c] : T(0);
+  const T tauj = coef[0], beta = coef[1], d = coef[2];
+  const bool has = coef[3] != T(0);
+  __syncthreads();
+  T* Pj = P + (size_t)j * ldp;
+  for (int rr = tid; rr < nr; rr += PT) {
+    const int i = r0 + rr;
+    if (i > j) {
+      T v = Pj[i];
+      if (has) v = tauj == T(0) ? T(0) : v / d;
+      Pj[i] = v;
+      vs[rr] = v;
+    } else if (i == j) {
+      if (has) Pj[j] = beta;
+      for (int c = j + 1; c < nc; ++c) P[j + (size_t)c * ldp] -= w[c];
+    }
+  }
+  __syncthreads();
+  for (int c = j + 1 + warp; c < nc; c += PT / 32) {
+    T* Pc = P + (size_t)c * ldp;
+    const T wc = w[c];
+    for (int rr = lane; rr < nr; rr += 32) {
+      const int i = r0 + rr;
+      if (i > j) Pc[i] -= wc * vs[rr];
+    }
+  }
+  if (j + 1 < nsteps) {
+    __syncthreads();
+    norms_and_pick<T>(j + 1, nsteps, a, P, part, piv, counter, w);
+  }
+}
+
+// ------------------------------------------------------------ T factor
+// T(0:j, j) = -tau_j T(0:j, 0:j) (V^T V)(0:j, j), T(j, j) = tau_j (Sec. 5.1),
+// one CTA, T kept in shared memory (kb <= 128) or global memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__ gram, int ldg, const T* tau, T* Tm,
+                                                   int ldt, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* St = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x;
+  T* W = use_smem ? St : Tm;
+  const int ldw = use_smem ? kb : ldt;
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e % kb, c = e / kb;
+    W[i + (size_t)c * ldw] = T(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const T tj = tau[j];
+    for (int i = tid; i < j; i += blockDim.x) {
+      T s = T(0);
+      for (int l = i; l < j; ++l) s += W[i + (size_t)l * ldw] * gram[l + (size_t)j * ldg];
+      W[i + (size_t)j * ldw] = -tj * s;
+    }
+    if (tid == 0) W[j + (size_t)j * ldw] = tj;
+    __syncthreads();
+  }
+  if (use_smem)
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      const int i = e % kb, c = e / kb;
+      Tm[i + (size_t)c * ldt] = St[i + (size_t)c * kb];
+    }
+}
+
+// ------------------------------------------------------------ helpers
+template <typename T>
+__global__ void k_copy_mat(int r, int cols, const T* __restrict__ s, int lds, T* __restrict__ d, int ldd) {
+  const int64_t n = (int64_t)r * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % r, j = e / r;
+    d[i + j * ldd] = s[i + j * lds];
+  }
+}
+
+template <typename T>
+__global__ void k_set_mat(int r, int cols, T val, T* d, int ldd) {
+  const int64_t n = (int64_t)r * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % r, j = e / r;
+    d[i + j * ldd] = val;
+  }
+}
+
+template <typename T>
+__global__ void k_make_vx(int mp, int kb, const T* __restrict__ F, int ldf, T* __restrict__ V, int ldv) {
+  const int64_t n = (int64_t)mp * kb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % mp), j = (int)(e / mp);
+    V[i + (int64_t)j * ldv] = i > j ? F[i + (int64_t)j * ldf] : (i == j ? T(1) : T(0));
+  }
+}
+
+int grid1d(int64_t n, int sms) {
+  int64_t g = (n + 255) / 256;
+  g = std::min<int64_t>(g, (int64_t)sms * 16);
+  return (int)std::max<int64_t>(g, 1);
+}
+
+void panel_geometry(int mp, int sms, int& C, int& R) {
+  // ~one CTA per SM for tall panels, at least 32 and at most 2048 rows per CTA
+  // (the step kernel keeps 2 R + nc values in dynamic shared memory)
+  C = std::max(1, std::min(sms, ceil_div(mp, 32)));
+  C = std::max(C, ceil_div(mp, 2048));
+  R = ceil_div(std::max(mp, 1), C);
+  C = ceil_div(std::max(mp, 1), R);
+}
+
+}  // namespace
+
+template <typename T>
+size_t panel_scratch_elems(int mp, int nc, int sms) {
+  int C, R;
+  panel_geometry(mp, sms, C, R);
+  // part [C][nc+1] + rowbuf[2][nc] + coef[2][NCOEF+nc] + counter/piv (as T) + slack
+  return (size_t)C * (nc + 1) + 2 * (size_t)nc + 2 * (size_t)(NCOEF + nc) + 2 * (size_t)nc + 64;
+}
+
+struct PanelScratch {};
+
+template <typename T>
+static void carve_panel(T* scratch, int C, int nc, T*& part, T*& rowbuf, T*& coef, int*& counter, int*& piv) {
+  part = scratch;
+  rowbuf = part + (size_t)C * (nc + 1);
+  coef = rowbuf + 2 * (size_t)nc;
+  T* tail = coef + 2 * (size_t)(NCOEF + nc);
+  // align tail to 16 bytes for the int area
+  uintptr_t p = reinterpret_cast<uintptr_t>(tail);
+  p = (p + 15) & ~uintptr_t(15);
+  counter = reinterpret_cast<int*>(p);
+  piv = counter + 4;
+}
+
+template <typename T>
+void panel_qr(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch) {
+  if (mp <= 0 || nc <= 0) return;
+  int C, R;
+  panel_geometry(mp, c.sms, C, R);
+  T *part, *rowbuf, *coef;
+  int *counter, *piv;
+  carve_panel(scratch, C, nc, part, rowbuf, coef, counter, piv);
+  cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
+  PanelArgs a{mp, nc, R, ldp};
+  const size_t sm_init = sizeof(T) * (size_t)nc;
+  const size_t sm_step = sizeof(T) * ((size_t)nc + 2 * (size_t)R);
+  k_panel_init<T><<<C, PT, sm_init, c.stream>>>(a, P, part, rowbuf, coef, tau, counter, c.status);
+  note_launch(c, 1 + nc);
+  for (int j = 0; j < nc; ++j) {
+    const T* cin = coef + (size_t)(j & 1) * (NCOEF + nc);
+    T* cout = coef + (size_t)((j + 1) & 1) * (NCOEF + nc);
+    T* rb = rowbuf + (size_t)((j + 1) & 1) * nc;
+    k_panel_step<T><<<C, PT, sm_step, c.stream>>>(j, a, P, cin, cout, part, rb, tau, counter, c.status);
+  }
+}
+
+template <typename T>
+void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int32_t* perm, T* tau, T* scratch) {
+  const int mp = m - r0;
+  if (mp <= 0 || nc <= 0) return;
+  const int nsteps = std::min(nc, mp - 1);
+  int C, R;
+  panel_geometry(mp, c.sms, C, R);
+  T *part, *rowbuf, *coef;
+  int *counter, *piv;
+  carve_panel(scratch, C, nc, part, rowbuf, coef, counter, piv);
+  cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
+  set_mat<T>(c, nc, 1, T(0), tau, nc);
+  PanelArgs a{mp, nc, R, lda};
+  T* P = A + r0 + (size_t)c0 * lda;
+  const size_t sm_small = sizeof(T) * (size_t)nc;
+  const size_t sm_apply = sizeof(T) * ((size_t)nc + (size_t)R);
+  if (nsteps <= 0) return;
+  // r0 == c0 for every caller (the block sits on the diagonal)
+  k_qrcp_init<T><<<C, PT, sm_small, c.stream>>>(a, P, part, piv, counter);
+  note_launch(c, 1 + 2 * (int64_t)nsteps);
+  for (int j = 0; j < nsteps; ++j) {
+    k_qrcp_pick<T><<<C, PT, sm_small, c.stream>>>(j, a, c0, m, A, lda, perm, piv, part, rowbuf, coef, tau, counter,
+                                                 c.status);
+    k_qrcp_apply<T><<<C, PT, sm_apply, c.stream>>>(j, nsteps, a, P, coef, part, piv, counter);
+  }
+}
+
+template <typename T>
+void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt) {
+  if (kb <= 0) return;
+  const size_t need = sizeof(T) * (size_t)kb * kb;
+  const int use_smem = need <= 200 * 1024 ? 1 : 0;
+  const size_t sm = use_smem ? need : 0;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_larft_tri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_larft_tri<T><<<1, 256, sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt, use_smem);
+  note_launch(c);
+}
+
+template <typename T>
+void copy_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd) {
+  if (r <= 0 || cols <= 0) return;
+  k_copy_mat<T><<<grid1d((int64_t)r * cols, c.sms), 256, 0, c.stream>>>(r, cols, src, lds, dst, ldd);
+  note_launch(c);
+}
+
+template <typename T>
+void set_mat(const Ctx& c, int r, int cols, T val, T* dst, int ldd) {
+  if (r <= 0 || cols <= 0) return;
+  k_set_mat<T><<<grid1d((int64_t)r * cols, c.sms), 256, 0, c.stream>>>(r, cols, val, dst, ldd);
+  note_launch(c);
+}
+
+template <typename T>
+void make_vx(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv) {
+  if (mp <= 0 || kb <= 0) return;
+  k_make_vx<T><<<grid1d((int64_t)mp * kb, c.sms), 256, 0, c.stream>>>(mp, kb, F, ldf, V, ldv);
+  note_launch(c);
+}
+
+#define RQR_INST(T)                                                                                      \
+  template size_t panel_scratch_elems<T>(int, int, int);                                                \
+  template void panel_qr<T>(const Ctx&, int, int, T*, int, T*, T*);                                       \
+  template void qrcp_block<T>(const Ctx&, int, int, int, int, T*, int, int32_t*, T*, T*);                 \
+  template void larft_tri<T>(const Ctx&, int, const T*, int, const T*, T*, int);                          \
+  template void copy_mat<T>(const Ctx&, int, int, const T*, int, T*, int);                                \
+  template void set_mat<T>(const Ctx&, int, int, T, T*, int);                                             \
+  template void make_vx<T>(const Ctx&, int, int, const T*, int, T*, int);
+RQR_INST(double)
+RQR_INST(float)
+#undef RQR_INST
+
+}  // namespace rqr

@@ -1,0 +1,244 @@
+"""Thin Python binding of the C ABI in include/rqr.h.
+
+Argument marshalling only: every step of the factorizations runs in the CUDA
+library librqr.so. PyTorch provides device memory (the caching allocator) and
+streams. Matrices are passed in column-major storage: a torch tensor ``A`` of
+shape (m, n) with strides (1, lda), e.g. ``colmajor(torch_tensor)``.
+
+The library must be built (``paper_1505_08115_gb300.build.build()``); when it
+is missing, or no CUDA device is present, every call raises RuntimeError.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "librqr.so")
+
+FP64, FP32 = 0, 1
+SKETCH_DOWNDATE, SKETCH_RESAMPLE = 0, 1
+STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 4: "workspace too small",
+          5: "unsupported combination", 6: "invalid handle"}
+
+# every symbol declared in include/rqr.h
+EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_workspace_bytes", "rqrcp_factor", "rurv_factor",
+           "rqr_form_q", "rqr_gauss_fill", "rqr_philox_raw", "rqr_profile_enable", "rqr_profile_read",
+           "rqr_version")
+PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final")
+
+_lock = threading.Lock()
+_lib = None
+_handles: dict[int, ctypes.c_void_p] = {}
+
+
+class RQRError(RuntimeError):
+    pass
+
+
+def load(path: str = SO_PATH):
+    """Loads librqr.so and declares the argument types of every entry point."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RQRError(f"{path} is missing: build it with paper_1505_08115_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i, u64, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_size_t
+        ip = ctypes.POINTER(ctypes.c_int)
+        u32 = ctypes.c_uint32
+        L.rqr_create.argtypes = [ctypes.POINTER(vp), vp]
+        L.rqr_destroy.argtypes = [vp]
+        L.rqr_set_stream.argtypes = [vp, vp]
+        L.rqr_workspace_bytes.argtypes = [i, i, i, i, i, i, i, ctypes.POINTER(sz)]
+        L.rqrcp_factor.argtypes = [vp, i, i, vp, i, i, i, u64, vp, i, vp, i, vp, i, i, vp, sz, ip]
+        L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, i, vp, sz, ip]
+        L.rqr_form_q.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i, vp, sz]
+        L.rqr_gauss_fill.argtypes = [vp, u64, u64, i64, vp, i]
+        L.rqr_philox_raw.argtypes = [vp, u32, u32, u32, u32, u32, i64, vp]
+        L.rqr_profile_enable.argtypes = [vp, i]
+        L.rqr_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64), i]
+        L.rqr_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "rqr_version":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _require_cuda(t: torch.Tensor):
+    if not t.is_cuda:
+        raise RQRError("tensors must live on a CUDA device")
+
+
+def handle(device: torch.device | None = None) -> ctypes.c_void_p:
+    """Per-device handle, rebound to torch's current stream on every call."""
+    L = load()
+    if not torch.cuda.is_available():
+        raise RQRError("no CUDA device: the randomized QR library has no CPU path")
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    with _lock:
+        h = _handles.get(dev)
+        if h is None:
+            h = ctypes.c_void_p()
+            with torch.cuda.device(dev):
+                rc = L.rqr_create(ctypes.byref(h), ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+            if rc != 0:
+                raise RQRError(f"rqr_create failed ({rc})")
+            _handles[dev] = h
+    L.rqr_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    return h
+
+
+def colmajor(A: torch.Tensor) -> torch.Tensor:
+    """Same values, column-major storage (strides (1, m))."""
+    return A.mT.contiguous().mT
+
+
+def empty_colmajor(m: int, n: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
+    return torch.empty((n, m), dtype=dtype, device=device).mT
+
+
+def _ld(A: torch.Tensor) -> int:
+    m, n = A.shape
+    if A.stride(0) != 1 or (n > 1 and A.stride(1) < max(1, m)):
+        raise RQRError("matrix must be column-major: shape (m, n) with strides (1, ld), ld >= m")
+    return max(A.stride(1), max(1, m)) if n > 0 else max(1, m)
+
+
+def _prec(dtype) -> int:
+    if dtype == torch.float64:
+        return FP64
+    if dtype == torch.float32:
+        return FP32
+    raise RQRError(f"unsupported dtype {dtype}")
+
+
+def workspace_bytes(m, n, b, p, q=-1, prec=FP64, sketch=SKETCH_DOWNDATE) -> int:
+    out = ctypes.c_size_t()
+    rc = load().rqr_workspace_bytes(m, n, b, p, q, prec, sketch, ctypes.byref(out))
+    if rc != 0:
+        raise RQRError(f"rqr_workspace_bytes: argument {-rc} invalid" if rc < 0 else f"status {rc}")
+    return int(out.value)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def rqrcp_factor(A: torch.Tensor, b: int, p: int, seed: int = 1505, G: torch.Tensor | None = None,
+                 sketch: int = SKETCH_DOWNDATE, T: torch.Tensor | None = None, perm: torch.Tensor | None = None,
+                 work: torch.Tensor | None = None, check: bool = True):
+    """Randomized blocked QRCP in place on A (column-major, on the GPU).
+
+    Returns (T, perm, info); A holds R above the diagonal and the Householder
+    vectors below. With check=False the call does not wait for the GPU and
+    info is None."""
+    _require_cuda(A)
+    m, n = A.shape
+    lda = _ld(A)
+    prec = _prec(A.dtype)
+    if T is None:
+        T = empty_colmajor(b, n, A.dtype, A.device)
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=A.device)
+    ldg = 0
+    if G is not None:
+        if sketch == SKETCH_DOWNDATE:
+            ldg = _ld(G)
+        if G.dtype != A.dtype:
+            raise RQRError("G must have A's dtype")
+    if work is None:
+        work = torch.empty(workspace_bytes(m, n, b, p, -1, prec, sketch), dtype=torch.uint8, device=A.device)
+    info = ctypes.c_int(0)
+    rc = load().rqrcp_factor(handle(A.device), m, n, _ptr(A), lda, b, p, seed, _ptr(G), ldg, _ptr(T), _ld(T),
+                             _ptr(perm), prec, sketch, _ptr(work), work.numel(), ctypes.byref(info) if check else None)
+    if rc < 0:
+        raise RQRError(f"rqrcp_factor: argument {-rc} invalid")
+    if rc > 0:
+        raise RQRError(f"rqrcp_factor: {STATUS.get(rc, rc)}")
+    return T, perm, (info.value if check else None)
+
+
+def rurv_factor(A: torch.Tensor, b: int, p: int, q: int, k: int = 0, seed: int = 1505,
+                G: torch.Tensor | None = None, work: torch.Tensor | None = None, check: bool = True):
+    """Blocked QR with orthonormal pivots. Returns (TU, WV, TV, info)."""
+    _require_cuda(A)
+    m, n = A.shape
+    prec = _prec(A.dtype)
+    TU = empty_colmajor(b, n, A.dtype, A.device)
+    TV = empty_colmajor(b, n, A.dtype, A.device)
+    WV = empty_colmajor(n, n, A.dtype, A.device)
+    if work is None:
+        work = torch.empty(workspace_bytes(m, n, b, p, q, prec), dtype=torch.uint8, device=A.device)
+    info = ctypes.c_int(0)
+    rc = load().rurv_factor(handle(A.device), m, n, _ptr(A), _ld(A), b, p, q, k, seed, _ptr(G), _ptr(TU), _ld(TU),
+                            _ptr(WV), _ld(WV), _ptr(TV), _ld(TV), prec, _ptr(work), work.numel(),
+                            ctypes.byref(info) if check else None)
+    if rc < 0:
+        raise RQRError(f"rurv_factor: argument {-rc} invalid")
+    if rc > 0:
+        raise RQRError(f"rurv_factor: {STATUS.get(rc, rc)}")
+    return TU, WV, TV, (info.value if check else None)
+
+
+def form_q(F: torch.Tensor, T: torch.Tensor, b: int, ncols: int | None = None, work: torch.Tensor | None = None):
+    """Explicit m x ncols Q from the block reflectors of a factor call."""
+    _require_cuda(F)
+    m, n = F.shape
+    ncols = m if ncols is None else ncols
+    prec = _prec(F.dtype)
+    Q = empty_colmajor(m, ncols, F.dtype, F.device)
+    if work is None:
+        work = torch.empty(workspace_bytes(m, n, b, 0, -1, prec), dtype=torch.uint8, device=F.device)
+    rc = load().rqr_form_q(handle(F.device), m, n, b, _ptr(F), _ld(F), _ptr(T), _ld(T), _ptr(Q), _ld(Q), ncols,
+                           prec, _ptr(work), work.numel())
+    if rc != 0:
+        raise RQRError(f"rqr_form_q failed ({rc})")
+    return Q
+
+
+def gauss_fill(seed: int, stream: int, count: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
+    out = torch.empty(count, dtype=dtype, device=device)
+    rc = load().rqr_gauss_fill(handle(out.device), seed, stream, count, _ptr(out), _prec(dtype))
+    if rc != 0:
+        raise RQRError(f"rqr_gauss_fill failed ({rc})")
+    return out
+
+
+def philox_raw(ctr0: int, ctr2: int, ctr3: int, key0: int, key1: int, count: int, device="cuda") -> torch.Tensor:
+    out = torch.empty(4 * count, dtype=torch.int32, device=device)
+    rc = load().rqr_philox_raw(handle(out.device), ctr0, ctr2, ctr3, key0, key1, count, _ptr(out))
+    if rc != 0:
+        raise RQRError(f"rqr_philox_raw failed ({rc})")
+    return out
+
+
+def profile_enable(on: bool = True, device=None) -> None:
+    """Per-phase CUDA-event tracing of the factor calls on this device."""
+    rc = load().rqr_profile_enable(handle(device), 1 if on else 0)
+    if rc != 0:
+        raise RQRError(f"rqr_profile_enable failed ({rc})")
+
+
+def profile_read(device=None) -> dict:
+    """{phase: {"ms": event time, "flops": algorithmic flops, "launches": kernels}}
+    since the last read (waits for the stream)."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    fl = (ctypes.c_double * n)()
+    ln = (ctypes.c_int64 * n)()
+    rc = load().rqr_profile_read(handle(device), ms, fl, ln, n)
+    if rc != 0:
+        raise RQRError(f"rqr_profile_read failed ({rc})")
+    return {p: {"ms": ms[i], "flops": fl[i], "launches": int(ln[i])} for i, p in enumerate(PHASES)}
+
+
+def version() -> str:
+    return load().rqr_version().decode()
