@@ -36,6 +36,9 @@ typedef struct rqr_handle_s* rqr_handle_t;
 /* Arithmetic of the factorization (the `prec` argument). */
 #define RQR_FP64 0 /* every step in FP64 (A, T are double) */
 #define RQR_FP32 1 /* every step in FP32 (A, T are float) */
+#define RQR_FP64X 2 /* FP64 data and FP64 panel/pivot/T steps; the large products
+                       (sketch, trailing update, downdate, Gram) are FP64-accurate
+                       splittings onto the bf16 tensor cores (Ozaki scheme) */
 
 /* How the sketch follows the factorization from block to block (`sketch`). */
 #define RQR_SKETCH_DOWNDATE 0 /* draw G once, update Y = G X after each block */
@@ -79,7 +82,8 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
  *   T        (device, out) b x n, ld ldt >= b: the block starting at column k0
  *            stores its upper-triangular T at T(0:b_i, k0:k0+b_i).
  *   perm     (device, out) n int32.
- *   prec     RQR_FP64 or RQR_FP32 (then A, G, T are float).
+ *   prec     RQR_FP64, RQR_FP64X (FP64 data, tensor-core products) or RQR_FP32
+ *            (then A, G, T are float).
  *   sketch   RQR_SKETCH_DOWNDATE or RQR_SKETCH_RESAMPLE.
  *   work     (device) workspace of lwork bytes, 256-byte aligned.
  *   info     (host, optional) see the header comment.
@@ -111,6 +115,16 @@ int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, in
 int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt,
                void* Q, int ldq, int ncols, int prec, void* work, size_t lwork);
 
+/* The dense products of the method, exposed for reuse and testing:
+ * C = alpha op(A) op(B) + beta C (column-major, op = transpose when ta / tb is
+ * non-zero; A is M x K or K x M, B is K x N or N x K, all device memory).
+ * prec RQR_FP64 (DMMA), RQR_FP32 (FFMA) or RQR_FP64X (bf16 tensor-core
+ * splitting with FP64 accuracy); alpha, beta are converted to the precision.
+ * work (device) of at least rqr_gemm_workspace_bytes bytes. */
+int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, double alpha, const void* A, int lda,
+             const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork);
+int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes);
+
 /* Fills out[0:count] (device) with N(0,1) samples: element e is lane e%4 of
  * Philox4x32-10 block e/4 with counter {lo(e/4), hi(e/4), lo(stream),
  * hi(stream)} and key {lo(seed), hi(seed)}, through Box-Muller on the pairs
@@ -125,14 +139,16 @@ int rqr_philox_raw(rqr_handle_t h, uint32_t ctr0, uint32_t ctr2, uint32_t ctr3, 
 
 /* Tracing: steps of the method timed with CUDA events on the handle's stream.
  * Phase indices for rqr_profile_read (paper section in brackets): */
-#define RQR_PHASE_SKETCH 0   /* Gaussian draw and Y = G A [Sec. 4.1]            */
-#define RQR_PHASE_PIVOT 1    /* b steps of Fig. QR on the sketch [Sec. 4.1, 4.3] */
+#define RQR_PHASE_SKETCH 0   /* Gaussian draw and Y = G A, power steps [Sec. 4.1, 6.3] */
+#define RQR_PHASE_PIVOT 1    /* pivots from the sketch: b steps of Fig. QR, or the
+                                orthonormal pivot (QR, l->b SVD) [Sec. 4.1-4.3] */
 #define RQR_PHASE_SWAP 2     /* column swaps of A, Y, perm [Fig. blockQR]        */
 #define RQR_PHASE_PANEL 3    /* panel Householder QR and T [Sec. 3.2, 5.1]       */
 #define RQR_PHASE_UPDATE 4   /* trailing update (I - V T V^T)^T A22 [Fig. blockQR] */
 #define RQR_PHASE_DOWNDATE 5 /* sketch downdate (not in the paper)               */
 #define RQR_PHASE_FINAL 6    /* last block by Fig. QR [Fig. blockQR, last step]  */
-#define RQR_NUM_PHASES 7
+#define RQR_PHASE_RIGHT 7    /* orthonormal pivot applied from the right [Fig. blockRRQR] */
+#define RQR_NUM_PHASES 8
 
 /* Turns per-phase event recording on (on != 0) or off and clears the counters. */
 int rqr_profile_enable(rqr_handle_t h, int on);

@@ -135,6 +135,25 @@ template <typename T>
 void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy,
                  int y0, int32_t* perm, T* tmp, int* imap);
 
+// FP64-accurate product on the bf16 tensor cores (ozaki.cu); iscr holds
+// ozaki_scratch_elems(M, N) ints.
+size_t ozaki_scratch_elems(int M, int N);
+void gemm_f64x(const Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
+               const double* B, int ldb, double beta, double* C, int ldc, int* iscr, double* part, size_t part_cap);
+
+// ---------------------------------------------------------------- small SVD
+// One-sided Jacobi on the r x cols matrix M (FP64, overwritten by M J); Js
+// (cols x nkeep) receives the columns of J with the nkeep largest norms of
+// M J, sv the sorted norms, order the column order; flags: 2 ints of scratch.
+void jacobi_svd(const Ctx& c, int r, int cols, double* M, int ldm, double* J, int ldj, int nkeep, double* Js,
+                int ldjs, double* sv, int* order, int* flags);
+// M (cols x kk) = R^T, R = upper triangle of the first kk rows of F.
+template <typename T>
+void r_transpose(const Ctx& c, int kk, int cols, const T* F, int ldf, T* M, int ldm);
+// Strictly lower part of src into dst, zeros elsewhere.
+template <typename T>
+void copy_lower(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
+
 }  // namespace rqr
 
 #define RQR_CUDA_TRY(x)                                  \

@@ -57,17 +57,38 @@ __device__ void reflector_coef(int j, int mp, T alpha, T s_below, T* coef, T* ta
 
 // Last-CTA step: totals of the partials for column jn (entry 0 = squared norm
 // below the diagonal, entry 1 + c = dot with column c) and its coefficients.
+// Lane l of every warp owns columns jn + l + 32k; warp w adds the partials of
+// CTAs w, w + 8, ... (independent loads, no long serial chain); the eight warp
+// sums are then added in warp order, so the result does not depend on timing.
 template <typename T>
 __device__ void finish_coef(int jn, const PanelArgs& a, const T* part, const T* rowbuf, T* coef, T* tau_out,
                             int* status, T* red) {
-  const int C = gridDim.x, tid = threadIdx.x, nc = a.nc;
-  for (int c = jn + tid; c < nc; c += PT) {
-    const int e = (c == jn) ? 0 : 1 + c;
-    T s = T(0);
-    for (int q = 0; q < C; ++q) s += __ldcg(part + (size_t)q * (nc + 1) + e);
-    red[c] = s;
+  constexpr int NW = PT / 32;
+  __shared__ T wred[NW][32 * 4];
+  const int C = gridDim.x, tid = threadIdx.x, nc = a.nc, lane = tid & 31, warp = tid >> 5;
+  for (int c0 = jn; c0 < nc; c0 += 32 * 4) {
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int q = warp; q < C; q += NW) {
+      const T* pq = part + (size_t)q * (nc + 1);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = c0 + lane + 32 * k;
+        if (c < nc) acc[k] += __ldcg(pq + (c == jn ? 0 : 1 + c));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) wred[warp][lane + 32 * k] = acc[k];
+    __syncthreads();
+    for (int t = tid; t < 32 * 4; t += PT) {
+      const int c = c0 + t;
+      if (c < nc) {
+        T s = T(0);
+        for (int w = 0; w < NW; ++w) s += wred[w][t];
+        red[c] = s;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid == 0) reflector_coef<T>(jn, a.mp, __ldcg(rowbuf + jn), red[jn], coef, tau_out, status);
   __syncthreads();
   const T tau = coef[0], d = coef[2];
@@ -141,72 +162,81 @@ __global__ void __launch_bounds__(PT) k_panel_init(PanelArgs a, const T* __restr
   }
 }
 
+// One column step. The CTA's rows >= j of the active columns j..nc-1 are
+// staged in shared memory with one parallel load (tile[cc*R + rr] holds
+// P(r0 + rr, j + cc)), updated there, and written back once.
 template <typename T>
 __global__ void __launch_bounds__(PT) k_panel_step(int j, PanelArgs a, T* __restrict__ P, const T* coef_in,
                                                    T* coef_out, T* part, T* rowbuf_out, T* tau, int* counter,
                                                    int* status) {
   extern __shared__ unsigned char smem_raw[];
-  T* w = reinterpret_cast<T*>(smem_raw);      // [nc]
-  T* vs = w + a.nc;                           // [R]
-  T* xn = vs + a.R;                           // [R]
+  const int nc = a.nc, ldp = a.ldp, R = a.R, wj = nc - j;
+  T* w = reinterpret_cast<T*>(smem_raw);  // [nc]
+  T* tile = w + nc;                       // [wj][R]
   __shared__ T wsum[PT / 32];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nc = a.nc, ldp = a.ldp;
-  const int r0 = q * a.R, r1 = min(a.mp, r0 + a.R), nr = max(0, r1 - r0);
+  const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
+  const int lo = min(nr, max(0, j - r0));  // first local row with global index >= j
+  const int h = nr - lo;
   for (int c = tid; c < nc; c += PT) w[c] = c > j ? coef_in[NCOEF + c] : T(0);
   const T tauj = coef_in[0], beta = coef_in[1], d = coef_in[2];
   const bool has = coef_in[3] != T(0);
+  for (int e = tid; e < h * wj; e += PT) {
+    const int rr = lo + e % h, cc = e / h;
+    tile[cc * R + rr] = P[r0 + rr + (size_t)(j + cc) * ldp];
+  }
   __syncthreads();
-  T* Pj = P + (size_t)j * ldp;
-  T* Pj1 = P + (size_t)(j + 1) * ldp;
-  const bool next = j + 1 < nc;
-  // column j -> v (rows > j); column j+1 updated (rows > j); row j finished
-  for (int rr = tid; rr < nr; rr += PT) {
+  // column j becomes v below the diagonal and beta on it
+  for (int rr = lo + tid; rr < nr; rr += PT) {
     const int i = r0 + rr;
     if (i > j) {
-      T v = Pj[i];
-      if (has) v = tauj == T(0) ? T(0) : v / d;
-      Pj[i] = v;
-      vs[rr] = v;
-      if (next) {
-        const T x = Pj1[i] - w[j + 1] * v;
-        Pj1[i] = x;
-        xn[rr] = x;
-        if (i == j + 1) rowbuf_out[j + 1] = x;
-      }
-    } else if (i == j) {
-      if (has) Pj[j] = beta;
-      for (int c = j + 1; c < nc; ++c) P[j + (size_t)c * ldp] -= w[c];
+      if (has) tile[rr] = tauj == T(0) ? T(0) : tile[rr] / d;
+    } else if (has) {
+      tile[rr] = beta;
     }
   }
   __syncthreads();
+  const bool next = j + 1 < nc;
   if (next) {
+    // column j+1 first: its updated values feed the dot products below
+    const T w1 = w[j + 1];
+    for (int rr = lo + tid; rr < nr; rr += PT) {
+      const int i = r0 + rr;
+      const T vi = i == j ? T(1) : tile[rr];
+      tile[R + rr] -= w1 * vi;
+    }
+    __syncthreads();
     T* myp = part + (size_t)q * (nc + 1);
     T s = T(0);
-    for (int rr = tid; rr < nr; rr += PT)
-      if (r0 + rr > j + 1) s += xn[rr] * xn[rr];
+    for (int rr = lo + tid; rr < nr; rr += PT)
+      if (r0 + rr > j + 1) s += tile[R + rr] * tile[R + rr];
     s = block_sum(s, wsum);
     if (tid == 0) myp[0] = s;
     for (int c = j + 2 + warp; c < nc; c += PT / 32) {
-      T* Pc = P + (size_t)c * ldp;
+      T* x = tile + (size_t)(c - j) * R;
       const T wc = w[c];
       T acc = T(0);
-      for (int rr = lane; rr < nr; rr += 32) {
+      for (int rr = lo + lane; rr < nr; rr += 32) {
         const int i = r0 + rr;
-        if (i > j) {
-          const T x = Pc[i] - wc * vs[rr];
-          Pc[i] = x;
-          if (i > j + 1) acc += xn[rr] * x;
-          else rowbuf_out[c] = x;
-        }
+        const T vi = i == j ? T(1) : tile[rr];
+        const T xv = x[rr] - wc * vi;
+        x[rr] = xv;
+        if (i > j + 1) acc += tile[R + rr] * xv;
       }
       acc = warp_sum(acc);
       if (lane == 0) myp[1 + c] = acc;
     }
-    if (last_cta(counter)) {
-      finish_coef<T>(j + 1, a, part, rowbuf_out, coef_out, tau, status, w);
-      if (tid == 0) *counter = 0;
-    }
+    __syncthreads();
+    if (j + 1 >= r0 && j + 1 < r1)
+      for (int c = j + 1 + tid; c < nc; c += PT) rowbuf_out[c] = tile[(size_t)(c - j) * R + (j + 1 - r0)];
+  }
+  for (int e = tid; e < h * wj; e += PT) {
+    const int rr = lo + e % h, cc = e / h;
+    P[r0 + rr + (size_t)(j + cc) * ldp] = tile[cc * R + rr];
+  }
+  if (next && last_cta(counter)) {
+    finish_coef<T>(j + 1, a, part, rowbuf_out, coef_out, tau, status, w);
+    if (tid == 0) *counter = 0;
   }
 }
 
@@ -427,11 +457,14 @@ int grid1d(int64_t n, int sms) {
   return (int)std::max<int64_t>(g, 1);
 }
 
-void panel_geometry(int mp, int sms, int& C, int& R) {
-  // ~one CTA per SM for tall panels, at least 32 and at most 2048 rows per CTA
-  // (the step kernel keeps 2 R + nc values in dynamic shared memory)
+constexpr size_t kPanelSmemBytes = 200 * 1024;
+
+// ~one CTA per SM for tall panels, at least 32 rows per CTA, and few enough
+// rows that the step kernel's tile (R x nc values) fits in shared memory.
+void panel_geometry(int mp, int nc, size_t elem, int sms, int& C, int& R) {
+  const int rmax = std::max(8, (int)std::min<size_t>(2048, (kPanelSmemBytes / elem - nc) / std::max(nc, 1)));
   C = std::max(1, std::min(sms, ceil_div(mp, 32)));
-  C = std::max(C, ceil_div(mp, 2048));
+  C = std::max(C, ceil_div(mp, rmax));
   R = ceil_div(std::max(mp, 1), C);
   C = ceil_div(std::max(mp, 1), R);
 }
@@ -441,7 +474,7 @@ void panel_geometry(int mp, int sms, int& C, int& R) {
 template <typename T>
 size_t panel_scratch_elems(int mp, int nc, int sms) {
   int C, R;
-  panel_geometry(mp, sms, C, R);
+  panel_geometry(mp, nc, sizeof(T), sms, C, R);
   // part [C][nc+1] + rowbuf[2][nc] + coef[2][NCOEF+nc] + counter/piv (as T) + slack
   return (size_t)C * (nc + 1) + 2 * (size_t)nc + 2 * (size_t)(NCOEF + nc) + 2 * (size_t)nc + 64;
 }
@@ -465,14 +498,16 @@ template <typename T>
 void panel_qr(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch) {
   if (mp <= 0 || nc <= 0) return;
   int C, R;
-  panel_geometry(mp, c.sms, C, R);
+  panel_geometry(mp, nc, sizeof(T), c.sms, C, R);
   T *part, *rowbuf, *coef;
   int *counter, *piv;
   carve_panel(scratch, C, nc, part, rowbuf, coef, counter, piv);
   cudaMemsetAsync(counter, 0, sizeof(int), c.stream);
   PanelArgs a{mp, nc, R, ldp};
   const size_t sm_init = sizeof(T) * (size_t)nc;
-  const size_t sm_step = sizeof(T) * ((size_t)nc + 2 * (size_t)R);
+  const size_t sm_step = sizeof(T) * ((size_t)nc + (size_t)nc * R);
+  if (sm_step > 48 * 1024)
+    cudaFuncSetAttribute(k_panel_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_step);
   k_panel_init<T><<<C, PT, sm_init, c.stream>>>(a, P, part, rowbuf, coef, tau, counter, c.status);
   note_launch(c, 1 + nc);
   for (int j = 0; j < nc; ++j) {
@@ -489,7 +524,7 @@ void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int3
   if (mp <= 0 || nc <= 0) return;
   const int nsteps = std::min(nc, mp - 1);
   int C, R;
-  panel_geometry(mp, c.sms, C, R);
+  panel_geometry(mp, nc, sizeof(T), c.sms, C, R);
   T *part, *rowbuf, *coef;
   int *counter, *piv;
   carve_panel(scratch, C, nc, part, rowbuf, coef, counter, piv);

@@ -55,47 +55,53 @@ __device__ void cta_best(T wn, int wp, T* shn, int* shp, T& bn, int& bp) {
     }
 }
 
-// Last CTA: global argmax over the CTA candidates, record the pick, and build
-// the reflector of the picked column (rows j..l-1 of buffer Yw, column pick).
+// Last CTA: global argmax over the CTA candidates (every thread scans a few,
+// then a fixed-order reduction in shared memory; largest norm, lowest position
+// on ties), record the pick, and build the reflector of the picked column
+// (rows j..l-1 of buffer Yw, column pick).
 template <typename T>
 __device__ void pick_and_reflect(int j, const YArgs& a, const T* cand_n, const int* cand_p, const T* Yw, int* picks,
                                  T* vbuf, int* counter) {
-  __shared__ int s_pick;
+  __shared__ T sn[YT];
+  __shared__ int sp[YT];
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid < 32) {
-    T bn = T(-1);
-    int bp = 0x7fffffff;
-    for (int q = lane; q < (int)gridDim.x; q += 32) {
-      const T n = __ldcg(cand_n + q);
-      const int p = __ldcg(cand_p + q);
-      if (n > bn || (n == bn && p < bp)) {
-        bn = n;
-        bp = p;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T on = __shfl_xor_sync(0xffffffffu, bn, o);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (on > bn || (on == bn && op < bp)) {
-        bn = on;
-        bp = op;
-      }
-    }
-    if (lane == 0) {
-      s_pick = bp;
-      picks[j] = bp;
+  T bn = T(-1);
+  int bp = 0x7fffffff;
+  for (int q = tid; q < (int)gridDim.x; q += YT) {
+    const T n = __ldcg(cand_n + q);
+    const int p = __ldcg(cand_p + q);
+    if (n > bn || (n == bn && p < bp)) {
+      bn = n;
+      bp = p;
     }
   }
+  sn[tid] = bn;
+  sp[tid] = bp;
   __syncthreads();
+  for (int half = YT / 2; half > 0; half >>= 1) {
+    if (tid < half) {
+      const T on = sn[tid + half];
+      const int op = sp[tid + half];
+      if (on > sn[tid] || (on == sn[tid] && op < sp[tid])) {
+        sn[tid] = on;
+        sp[tid] = op;
+      }
+    }
+    __syncthreads();
+  }
+  const int pick = sp[0];
+  if (tid == 0) picks[j] = pick;
   // reflector of Yw(j:l, pick): alpha, norm, v = y / (alpha - beta), tau
   if (tid < 32) {
-    const T* y = Yw + (size_t)s_pick * a.l;
+    const T* y = Yw + (size_t)pick * a.l;
     const int L = a.l - j;
     T s = T(0);
-    for (int r = lane; r < L; r += 32) s += y[j + r] * y[j + r];
+    for (int r = lane; r < L; r += 32) {
+      const T x = __ldcg(y + j + r);
+      s += x * x;
+    }
     s = warp_sum(s);
-    const T alpha = y[j];
+    const T alpha = __ldcg(y + j);
     T tau = T(0), d = T(1);
     if (L >= 2 && s > T(0)) {
       const T beta = -sgn0(alpha) * sqrt(s);
@@ -303,8 +309,10 @@ __global__ void k_scatter(const int* imap, int m, T* A, int lda, int k0, int l, 
   if (blockIdx.x == 0 && threadIdx.x == 0) perm[k0 + dst] = tmpP[t];
 }
 
+// Four CTAs per SM: each warp then handles only a few positions per step, so
+// the chain of dependent L2 round trips inside a step stays short.
 void ygeometry(int np, int sms, int& C, int& per) {
-  C = std::max(1, std::min(sms, ceil_div(np, 16)));
+  C = std::max(1, std::min(4 * sms, ceil_div(np, 8)));
   per = ceil_div(std::max(np, 1), C);
   C = ceil_div(std::max(np, 1), per);
 }

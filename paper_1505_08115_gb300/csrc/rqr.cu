@@ -91,8 +91,30 @@ size_t gemm_cap(int sms) { return (size_t)8 * sms * 64 * 64; }
 template <typename T>
 struct RqrcpWs {
   T *Y, *Gc, *Vx, *W, *W2, *gram, *GV, *GVT, *tau, *part, *pscr, *yscr, *swp;
-  int *picks, *imap;
+  int *picks, *imap, *iscr;
   size_t part_cap;
+};
+
+// Dense product of the method: native precision, or (FP64 with emu) the
+// FP64-accurate bf16 tensor-core splitting of ozaki.cu for products large
+// enough to pay for the splitting.
+template <typename T>
+struct Gemm {
+  const rqr::Ctx& c;
+  bool emu;
+  int* iscr;
+  T* part;
+  size_t cap;
+  void operator()(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, const T* B, int ldb, T beta,
+                  T* C, int ldc) const {
+    if constexpr (sizeof(T) == 8) {
+      if (emu && (double)M * N * K >= 4.0e6 && M >= 16 && N >= 16 && K >= 16) {
+        rqr::gemm_f64x(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, iscr, part, cap);
+        return;
+      }
+    }
+    rqr::gemm<T>(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, part, cap);
+  }
 };
 
 template <typename T>
@@ -114,6 +136,7 @@ size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs
   w.swp = cv.take<T>((size_t)(std::max(m, 1) + l) * 2 * b + 2 * (size_t)b + 16);
   w.picks = cv.take<int>((size_t)b);
   w.imap = cv.take<int>(1 + 4 * (size_t)b + 8);
+  w.iscr = cv.take<int>(rqr::ozaki_scratch_elems(std::max(m, l), std::max(n, m)));
   return cv.used;
 }
 
@@ -145,7 +168,7 @@ int finish(rqr_handle_t h, int* info) {
 
 template <typename T>
 int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64_t seed, const T* G, int ldg, T* Tm,
-               int ldt, int32_t* perm, int sketch, void* work, size_t lwork, int* info) {
+               int ldt, int32_t* perm, int sketch, bool emu, void* work, size_t lwork, int* info) {
   using namespace rqr;
   const int l = b + p;
   Carver cv{static_cast<char*>(work), lwork, 0, false};
@@ -153,6 +176,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
   carve_rqrcp<T>(cv, m, n, b, p, h->sms, w);
   if (!cv.ok()) return RQR_ERR_WORKSPACE;
   Ctx c = make_ctx(h);
+  const Gemm<T> mm{c, emu, w.iscr, w.part, w.part_cap};
   cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
   if (n == 0) return finish(h, info);
   const bool down = sketch == RQR_SKETCH_DOWNDATE;
@@ -164,7 +188,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
     if (down && n > b) {
       if (G) copy_mat<T>(c, l, m, G, ldg, w.Gc, l);
       else gauss_fill_2d<T>(c, seed, 0, l, m, w.Gc, l);
-      gemm<T>(c, false, false, l, n, m, T(1), w.Gc, l, A, lda, T(0), w.Y, l, w.part, w.part_cap);
+      mm(false, false, l, n, m, T(1), w.Gc, l, A, lda, T(0), w.Y, l);
     }
   }
   size_t goff = 0;
@@ -178,7 +202,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_FINAL, 2.0 * mp * np * (double)np - 2.0 * np * (double)np * np / 3.0);
       qrcp_block<T>(c, m, k0, k0, np, A, lda, perm, w.tau, w.pscr);
       make_vx<T>(c, mp, np, P, lda, w.Vx, mp);
-      gemm<T>(c, true, false, np, np, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, np, w.part, w.part_cap);
+      mm(true, false, np, np, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, np);
       larft_tri<T>(c, np, w.gram, np, w.tau, Tb, ldt);
       break;
     }
@@ -192,7 +216,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
         gauss_fill_2d<T>(c, seed, (uint64_t)blk, l, mp, w.Gc, l);
         Gi = w.Gc;
       }
-      gemm<T>(c, false, false, l, np, mp, T(1), Gi, l, P, lda, T(0), w.Y + (size_t)k0 * l, l, w.part, w.part_cap);
+      mm(false, false, l, np, mp, T(1), Gi, l, P, lda, T(0), w.Y + (size_t)k0 * l, l);
     }
     // (b) pivots from the sketch, (c) swaps
     {
@@ -208,7 +232,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)b * b - 2.0 * b * (double)b * b / 3.0);
       panel_qr<T>(c, mp, b, P, lda, w.tau, w.pscr);
       make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
-      gemm<T>(c, true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b, w.part, w.part_cap);
+      mm(true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b);
       larft_tri<T>(c, b, w.gram, b, w.tau, Tb, ldt);
     }
     // (e) trailing update
@@ -216,18 +240,18 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
     T* A2 = A + k0 + (size_t)(k0 + b) * lda;
     {
       Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * b);
-      gemm<T>(c, true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(0), w.W, b, w.part, w.part_cap);
-      gemm<T>(c, true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b, w.part, w.part_cap);
-      gemm<T>(c, false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda, w.part, w.part_cap);
+      mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(0), w.W, b);
+      mm(true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b);
+      mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);
     }
     if (down) {
       Phase ph(h, RQR_PHASE_DOWNDATE, 4.0 * l * mp * (double)b + 2.0 * l * b * (double)n2);
       T* Gk = w.Gc + (size_t)k0 * l;
-      gemm<T>(c, false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(0), w.GV, l, w.part, w.part_cap);
-      gemm<T>(c, false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l, w.part, w.part_cap);
-      gemm<T>(c, false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l, w.part, w.part_cap);
-      gemm<T>(c, false, false, l, n2, b, T(-1), Gk, l, A + k0 + (size_t)(k0 + b) * lda, lda, T(1),
-              w.Y + (size_t)(k0 + b) * l, l, w.part, w.part_cap);
+      mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(0), w.GV, l);
+      mm(false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l);
+      mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);
+      mm(false, false, l, n2, b, T(-1), Gk, l, A + k0 + (size_t)(k0 + b) * lda, lda, T(1),
+              w.Y + (size_t)(k0 + b) * l, l);
     }
     k0 += b;
     ++blk;
@@ -268,6 +292,152 @@ int form_q_impl(rqr_handle_t h, int m, int n, int b, const T* F, int ldf, const 
   }
   delete[] starts;
   return finish(h, nullptr);
+}
+
+
+struct RurvWs {
+  double *Z, *Qz, *Wm, *Qw, *Vx, *gram, *Tz, *W1, *Mj, *Jm, *Js, *sv, *Zr, *P1, *P2, *W, *W2, *tau, *part, *pscr;
+  int *order, *flags;
+  size_t part_cap;
+};
+
+size_t carve_rurv(rqr::Carver& cv, int m, int n, int b, int p, int sms, RurvWs& w) {
+  const int l = b + p;
+  const size_t mm = std::max(m, 1), nn = std::max(n, 1), mx = std::max(mm, nn);
+  w.Z = cv.take<double>(nn * l);
+  w.Qz = cv.take<double>(nn * l);
+  w.Wm = cv.take<double>(mm * l);
+  w.Qw = cv.take<double>(mm * l);
+  w.Vx = cv.take<double>(mx * l);
+  w.gram = cv.take<double>((size_t)l * l);
+  w.Tz = cv.take<double>((size_t)l * l);
+  w.W1 = cv.take<double>((size_t)l * l);
+  w.Mj = cv.take<double>((size_t)l * l);
+  w.Jm = cv.take<double>((size_t)l * l);
+  w.Js = cv.take<double>((size_t)l * b);
+  w.sv = cv.take<double>((size_t)l);
+  w.Zr = cv.take<double>(nn * b);
+  w.P1 = cv.take<double>(mm * b);
+  w.P2 = cv.take<double>(mm * b);
+  w.W = cv.take<double>((size_t)b * nn);
+  w.W2 = cv.take<double>((size_t)b * nn);
+  w.tau = cv.take<double>((size_t)l);
+  w.part_cap = gemm_cap(sms);
+  w.part = cv.take<double>(w.part_cap);
+  w.pscr = cv.take<double>(rqr::panel_scratch_elems<double>((int)mx, l, sms));
+  w.order = cv.take<int>((size_t)l);
+  w.flags = cv.take<int>(8);
+  return cv.used;
+}
+
+// Q (r x kq) = (I - V T V^T)[I_kq; 0] from a panel factored in place (r x cc).
+void form_thin_q(const rqr::Ctx& c, int r, int cc, int kq, const double* F, int ldf, const double* tau, RurvWs& w,
+                 double* Q, int ldq) {
+  using namespace rqr;
+  make_vx<double>(c, r, cc, F, ldf, w.Vx, r);
+  gemm<double>(c, true, false, cc, cc, r, 1.0, w.Vx, r, w.Vx, r, 0.0, w.gram, cc, w.part, w.part_cap);
+  larft_tri<double>(c, cc, w.gram, cc, tau, w.Tz, cc);
+  gemm<double>(c, false, true, cc, kq, cc, 1.0, w.Tz, cc, w.Vx, r, 0.0, w.W1, cc, w.part, w.part_cap);
+  set_mat<double>(c, r, kq, 0.0, Q, ldq);
+  set_mat<double>(c, 1, std::min(r, kq), 1.0, Q, ldq + 1);
+  gemm<double>(c, false, false, r, kq, cc, -1.0, w.Vx, r, w.W1, cc, 1.0, Q, ldq, w.part, w.part_cap);
+}
+
+int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, int q, int k, uint64_t seed,
+              const double* G, double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, void* work,
+              size_t lwork, int* info) {
+  using namespace rqr;
+  const int l = b + p;
+  Carver cv{static_cast<char*>(work), lwork, 0, false};
+  RurvWs w;
+  carve_rurv(cv, m, n, b, p, h->sms, w);
+  if (!cv.ok()) return RQR_ERR_WORKSPACE;
+  Ctx c = make_ctx(h);
+  cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
+  if (n == 0) return finish(h, info);
+  set_mat<double>(c, b, n, 0.0, TU, ldtu);
+  set_mat<double>(c, b, n, 0.0, TV, ldtv);
+  set_mat<double>(c, n, n, 0.0, WV, ldwv);
+  size_t goff = 0;
+  int k0 = 0, blk = 0;
+  while (k0 < n) {
+    const int np = n - k0, mp = m - k0, bi = std::min(b, np);
+    double* X = A + k0 + (size_t)k0 * lda;
+    int zc = l;
+    {
+      // Sec. 4.2 / 6.3: Z = X^T Omega, then q power steps with orthonormalisation
+      Phase ph(h, RQR_PHASE_SKETCH, (2.0 * q + 1.0) * 2.0 * l * mp * (double)np);
+      const double* Gi;
+      if (G) {
+        Gi = G + goff;
+        goff += (size_t)l * mp;
+      } else {
+        gauss_fill_2d<double>(c, seed, (uint64_t)blk, l, mp, w.Qw, l);
+        Gi = w.Qw;
+      }
+      gemm<double>(c, true, true, np, l, mp, 1.0, X, lda, Gi, l, 0.0, w.Z, np, w.part, w.part_cap);
+      for (int t = 0; t < q; ++t) {
+        const int kz = std::min(np, zc);
+        panel_qr<double>(c, np, zc, w.Z, np, w.tau, w.pscr);
+        form_thin_q(c, np, zc, kz, w.Z, np, w.tau, w, w.Qz, np);
+        gemm<double>(c, false, false, mp, kz, np, 1.0, X, lda, w.Qz, np, 0.0, w.Wm, mp, w.part, w.part_cap);
+        const int kw = std::min(mp, kz);
+        panel_qr<double>(c, mp, kz, w.Wm, mp, w.tau, w.pscr);
+        form_thin_q(c, mp, kz, kw, w.Wm, mp, w.tau, w, w.Qw, mp);
+        gemm<double>(c, true, false, np, kw, mp, 1.0, X, lda, w.Qw, mp, 0.0, w.Z, np, w.part, w.part_cap);
+        zc = kw;
+      }
+    }
+    double* TS = TV + (size_t)k0 * ldtv;
+    double* Wb = WV + k0 + (size_t)k0 * ldwv;
+    {
+      // l -> b_i reduction through the SVD of R_z, then Householder QR of Z
+      Phase ph(h, RQR_PHASE_PIVOT, 2.0 * np * (double)zc * zc + 2.0 * np * (double)bi * bi);
+      double* Zb = w.Z;
+      if (zc > bi) {
+        const int kk = std::min(np, zc);
+        panel_qr<double>(c, np, zc, w.Z, np, w.tau, w.pscr);
+        form_thin_q(c, np, zc, kk, w.Z, np, w.tau, w, w.Qz, np);
+        r_transpose<double>(c, kk, zc, w.Z, np, w.Mj, zc);
+        jacobi_svd(c, zc, kk, w.Mj, zc, w.Jm, kk, bi, w.Js, kk, w.sv, w.order, w.flags);
+        gemm<double>(c, false, false, np, bi, kk, 1.0, w.Qz, np, w.Js, kk, 0.0, w.Zr, np, w.part, w.part_cap);
+        Zb = w.Zr;
+      }
+      panel_qr<double>(c, np, bi, Zb, np, w.tau, w.pscr);
+      copy_lower<double>(c, np, bi, Zb, np, Wb, ldwv);
+      make_vx<double>(c, np, bi, Zb, np, w.Vx, np);
+      gemm<double>(c, true, false, bi, bi, np, 1.0, w.Vx, np, w.Vx, np, 0.0, w.gram, bi, w.part, w.part_cap);
+      larft_tri<double>(c, bi, w.gram, bi, w.tau, TS, ldtv);
+    }
+    {
+      // A(0:m, k0:n) <- A(0:m, k0:n) (I - W TS W^T), all m rows (Fig. blockRRQR)
+      Phase ph(h, RQR_PHASE_RIGHT, 4.0 * m * (double)np * bi);
+      double* Ak = A + (size_t)k0 * lda;
+      gemm<double>(c, false, false, m, bi, np, 1.0, Ak, lda, w.Vx, np, 0.0, w.P1, m, w.part, w.part_cap);
+      gemm<double>(c, false, false, m, bi, bi, 1.0, w.P1, m, TS, ldtv, 0.0, w.P2, m, w.part, w.part_cap);
+      gemm<double>(c, false, true, m, np, bi, -1.0, w.P2, m, w.Vx, np, 1.0, Ak, lda, w.part, w.part_cap);
+    }
+    double* Tb = TU + (size_t)k0 * ldtu;
+    {
+      Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)bi * bi - 2.0 * bi * (double)bi * bi / 3.0);
+      panel_qr<double>(c, mp, bi, X, lda, w.tau, w.pscr);
+      make_vx<double>(c, mp, bi, X, lda, w.Vx, mp);
+      gemm<double>(c, true, false, bi, bi, mp, 1.0, w.Vx, mp, w.Vx, mp, 0.0, w.gram, bi, w.part, w.part_cap);
+      larft_tri<double>(c, bi, w.gram, bi, w.tau, Tb, ldtu);
+    }
+    const int n2 = np - bi;
+    if (n2 > 0) {
+      Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * bi);
+      double* A2 = A + k0 + (size_t)(k0 + bi) * lda;
+      gemm<double>(c, true, false, bi, n2, mp, 1.0, w.Vx, mp, A2, lda, 0.0, w.W, bi, w.part, w.part_cap);
+      gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
+      gemm<double>(c, false, false, mp, n2, bi, -1.0, w.Vx, mp, w.W2, bi, 1.0, A2, lda, w.part, w.part_cap);
+    }
+    k0 += bi;
+    ++blk;
+    if (k > 0 && k0 >= k) break;
+  }
+  return finish(h, info);
 }
 
 }  // namespace
@@ -315,21 +485,24 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
   if (n < 0 || n > m) return -2;
   if (b < 1 || b > 512) return -3;
   if (p < 0) return -4;
-  if (prec != RQR_FP64 && prec != RQR_FP32) return -6;
+  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -6;
   if (sketch != RQR_SKETCH_DOWNDATE && sketch != RQR_SKETCH_RESAMPLE) return -7;
   if (!bytes) return -8;
   int dev = 0, sms = rqr::kNumSMs;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   rqr::Carver cv{nullptr, 0, 0, true};
-  if (prec == RQR_FP64) {
+  if (q >= 0) {
+    if (prec != RQR_FP64) return -6;
+    RurvWs w;
+    carve_rurv(cv, m, n, b, p, sms, w);
+  } else if (prec != RQR_FP32) {
     RqrcpWs<double> w;
     carve_rqrcp<double>(cv, m, n, b, p, sms, w);
   } else {
     RqrcpWs<float> w;
     carve_rqrcp<float>(cv, m, n, b, p, sms, w);
   }
-  (void)q;
   *bytes = cv.used + 256;
   return RQR_OK;
 }
@@ -347,25 +520,42 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
   if (!T && n > 0) return -11;
   if (ldt < b) return -12;
   if (!perm && n > 0) return -13;
-  if (prec != RQR_FP64 && prec != RQR_FP32) return -14;
+  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -14;
   if (sketch != RQR_SKETCH_DOWNDATE && sketch != RQR_SKETCH_RESAMPLE) return -15;
   if (!work && n > 0) return -16;
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -16;
   cudaGetLastError();
-  if (prec == RQR_FP64)
+  if (prec != RQR_FP32)
     return rqrcp_impl<double>(h, m, n, static_cast<double*>(A), lda, b, p, seed, static_cast<const double*>(G), ldg,
-                              static_cast<double*>(T), ldt, perm, sketch, work, lwork, info);
+                              static_cast<double*>(T), ldt, perm, sketch, prec == RQR_FP64X, work, lwork, info);
   return rqrcp_impl<float>(h, m, n, static_cast<float*>(A), lda, b, p, seed, static_cast<const float*>(G), ldg,
-                           static_cast<float*>(T), ldt, perm, sketch, work, lwork, info);
+                           static_cast<float*>(T), ldt, perm, sketch, false, work, lwork, info);
 }
 
 int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k, uint64_t seed,
                 const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV, int ldtv, int prec, void* work,
                 size_t lwork, int* info) {
-  (void)h; (void)m; (void)n; (void)A; (void)lda; (void)b; (void)p; (void)q; (void)k; (void)seed; (void)G;
-  (void)TU; (void)ldtu; (void)WV; (void)ldwv; (void)TV; (void)ldtv; (void)prec; (void)work; (void)lwork;
-  if (info) *info = RQR_ERR_UNSUPPORTED;
-  return RQR_ERR_UNSUPPORTED;
+  if (!valid(h)) return -1;
+  if (m < 0) return -2;
+  if (n < 0 || n > m) return -3;
+  if (!A && n > 0) return -4;
+  if (lda < std::max(1, m)) return -5;
+  if (b < 1 || b > 512) return -6;
+  if (p < 0 || b + p > 1024) return -7;
+  if (q < 0 || q > 64) return -8;
+  if (!TU && n > 0) return -12;
+  if (ldtu < b) return -13;
+  if (!WV && n > 0) return -14;
+  if (ldwv < std::max(1, n)) return -15;
+  if (!TV && n > 0) return -16;
+  if (ldtv < b) return -17;
+  if (prec != RQR_FP64) return -18;
+  if (!work && n > 0) return -19;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -19;
+  cudaGetLastError();
+  return rurv_impl(h, m, n, static_cast<double*>(A), lda, b, p, q, k, seed, static_cast<const double*>(G),
+                   static_cast<double*>(TU), ldtu, static_cast<double*>(WV), ldwv, static_cast<double*>(TV), ldtv,
+                   work, lwork, info);
 }
 
 int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt, void* Q, int ldq,
@@ -447,6 +637,62 @@ int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launche
     if (launches) launches[i] = p.launches[i];
   }
   return rqr_profile_enable(h, p.on);
+}
+
+int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, double alpha, const void* A, int lda,
+             const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork) {
+  if (!valid(h)) return -1;
+  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -2;
+  if (M < 0) return -5;
+  if (N < 0) return -6;
+  if (K < 0) return -7;
+  const int ar = ta ? K : M, br = tb ? N : K;
+  if (!A && M > 0 && K > 0) return -9;
+  if (lda < std::max(1, ar)) return -10;
+  if (!B && N > 0 && K > 0) return -11;
+  if (ldb < std::max(1, br)) return -12;
+  if (!C && M > 0 && N > 0) return -14;
+  if (ldc < std::max(1, M)) return -15;
+  size_t need = 0;
+  rqr_gemm_workspace_bytes(prec, M, N, K, &need);
+  if (lwork < need || (need > 0 && !work)) return RQR_ERR_WORKSPACE;
+  cudaGetLastError();
+  rqr::Ctx c = make_ctx(h);
+  rqr::Carver cv{static_cast<char*>(work), lwork, 0, false};
+  if (prec == RQR_FP32) {
+    const size_t cap = gemm_cap(h->sms);
+    float* part = cv.take<float>(cap);
+    rqr::gemm<float>(c, ta != 0, tb != 0, M, N, K, (float)alpha, static_cast<const float*>(A), lda,
+                     static_cast<const float*>(B), ldb, (float)beta, static_cast<float*>(C), ldc, part, cap);
+  } else {
+    const size_t cap = gemm_cap(h->sms);
+    double* part = cv.take<double>(cap);
+    int* iscr = cv.take<int>(rqr::ozaki_scratch_elems(M, N));
+    const Gemm<double> mm{c, prec == RQR_FP64X, iscr, part, cap};
+    if (prec == RQR_FP64X && M > 0 && N > 0 && K > 0)
+      rqr::gemm_f64x(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
+                     static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, iscr, part, cap);
+    else
+      mm(ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda, static_cast<const double*>(B), ldb,
+         beta, static_cast<double*>(C), ldc);
+  }
+  return finish(h, nullptr);
+}
+
+int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes) {
+  if (!bytes) return -5;
+  (void)K;
+  int dev = 0, sms = rqr::kNumSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  rqr::Carver cv{nullptr, 0, 0, true};
+  if (prec == RQR_FP32) cv.take<float>(gemm_cap(sms));
+  else {
+    cv.take<double>(gemm_cap(sms));
+    cv.take<int>(rqr::ozaki_scratch_elems(std::max(M, 0), std::max(N, 0)));
+  }
+  *bytes = cv.used;
+  return RQR_OK;
 }
 
 const char* rqr_version(void) { return "rqr-gb300 0.1 (sm_103a)"; }

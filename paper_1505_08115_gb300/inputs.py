@@ -165,10 +165,28 @@ def batch_shapes(count: int, seed: int = 1505, lo: int = 32, hi: int = 512):
 
 
 # ------------------------------------------------------------ GPU-side draws
+def _preload_torch_linalg():
+    """torch loads its CUDA linear-algebra library lazily by name; under a
+    profiler's injection that lookup can fail, so load it by path first."""
+    import ctypes
+    import glob
+    import os
+
+    import torch
+
+    for so in glob.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg*.so")):
+        try:
+            ctypes.CDLL(so, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def torch_svd_matrix(m: int, n: int, s, seed: int, device="cuda"):
     """U diag(s) V^T drawn on the device; returns an m x n FP64 tensor with
     column-major storage (shape (m, n), strides (1, m))."""
     import torch
+
+    _preload_torch_linalg()
 
     g = torch.Generator(device=device)
     g.manual_seed(seed)
@@ -191,6 +209,8 @@ def torch_svd_matrix(m: int, n: int, s, seed: int, device="cuda"):
 
 def torch_spike_matrix(n: int, seed: int, rank: int = 200, device="cuda", dtype=None):
     import torch
+
+    _preload_torch_linalg()
 
     g = torch.Generator(device=device)
     g.manual_seed(seed)

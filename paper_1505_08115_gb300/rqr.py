@@ -20,16 +20,16 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "librqr.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP64X = 0, 1, 2
 SKETCH_DOWNDATE, SKETCH_RESAMPLE = 0, 1
 STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 4: "workspace too small",
           5: "unsupported combination", 6: "invalid handle"}
 
 # every symbol declared in include/rqr.h
 EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_workspace_bytes", "rqrcp_factor", "rurv_factor",
-           "rqr_form_q", "rqr_gauss_fill", "rqr_philox_raw", "rqr_profile_enable", "rqr_profile_read",
-           "rqr_version")
-PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final")
+           "rqr_form_q", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill", "rqr_philox_raw",
+           "rqr_profile_enable", "rqr_profile_read", "rqr_version")
+PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final", "right")
 
 _lock = threading.Lock()
 _lib = None
@@ -59,6 +59,8 @@ def load(path: str = SO_PATH):
         L.rqrcp_factor.argtypes = [vp, i, i, vp, i, i, i, u64, vp, i, vp, i, vp, i, i, vp, sz, ip]
         L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, i, vp, sz, ip]
         L.rqr_form_q.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i, vp, sz]
+        L.rqr_gemm.argtypes = [vp, i, i, i, i, i, i, ctypes.c_double, vp, i, vp, i, ctypes.c_double, vp, i, vp, sz]
+        L.rqr_gemm_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(sz)]
         L.rqr_gauss_fill.argtypes = [vp, u64, u64, i64, vp, i]
         L.rqr_philox_raw.argtypes = [vp, u32, u32, u32, u32, u32, i64, vp]
         L.rqr_profile_enable.argtypes = [vp, i]
@@ -112,9 +114,9 @@ def _ld(A: torch.Tensor) -> int:
     return max(A.stride(1), max(1, m)) if n > 0 else max(1, m)
 
 
-def _prec(dtype) -> int:
+def _prec(dtype, emulated: bool = False) -> int:
     if dtype == torch.float64:
-        return FP64
+        return FP64X if emulated else FP64
     if dtype == torch.float32:
         return FP32
     raise RQRError(f"unsupported dtype {dtype}")
@@ -134,16 +136,17 @@ def _ptr(t):
 
 def rqrcp_factor(A: torch.Tensor, b: int, p: int, seed: int = 1505, G: torch.Tensor | None = None,
                  sketch: int = SKETCH_DOWNDATE, T: torch.Tensor | None = None, perm: torch.Tensor | None = None,
-                 work: torch.Tensor | None = None, check: bool = True):
+                 work: torch.Tensor | None = None, check: bool = True, emulated: bool = False):
     """Randomized blocked QRCP in place on A (column-major, on the GPU).
 
     Returns (T, perm, info); A holds R above the diagonal and the Householder
     vectors below. With check=False the call does not wait for the GPU and
-    info is None."""
+    info is None. emulated=True (FP64 only) runs the large products as
+    FP64-accurate bf16 tensor-core splittings (RQR_FP64X)."""
     _require_cuda(A)
     m, n = A.shape
     lda = _ld(A)
-    prec = _prec(A.dtype)
+    prec = _prec(A.dtype, emulated)
     if T is None:
         T = empty_colmajor(b, n, A.dtype, A.device)
     if perm is None:
@@ -202,6 +205,28 @@ def form_q(F: torch.Tensor, T: torch.Tensor, b: int, ncols: int | None = None, w
     if rc != 0:
         raise RQRError(f"rqr_form_q failed ({rc})")
     return Q
+
+
+def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, ta: bool = False, tb: bool = False,
+         alpha: float = 1.0, beta: float = 0.0, emulated: bool = False) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C through the library's product kernels
+    (column-major tensors; FP64 DMMA, FP32 FFMA, or emulated FP64)."""
+    _require_cuda(A)
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    prec = _prec(A.dtype, emulated)
+    if C is None:
+        C = empty_colmajor(M, N, A.dtype, A.device)
+        beta = 0.0
+    sz = ctypes.c_size_t()
+    load().rqr_gemm_workspace_bytes(prec, M, N, K, ctypes.byref(sz))
+    work = torch.empty(max(1, sz.value), dtype=torch.uint8, device=A.device)
+    rc = load().rqr_gemm(handle(A.device), prec, int(ta), int(tb), M, N, K, alpha, _ptr(A), _ld(A), _ptr(B), _ld(B),
+                         beta, _ptr(C), _ld(C), _ptr(work), work.numel())
+    if rc != 0:
+        raise RQRError(f"rqr_gemm failed ({rc})")
+    return C
 
 
 def gauss_fill(seed: int, stream: int, count: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
