@@ -51,6 +51,7 @@ typedef struct rqr_handle_s* rqr_handle_t;
 #define RQR_ERR_WORKSPACE 4   /* lwork smaller than rqr_workspace_bytes        */
 #define RQR_ERR_UNSUPPORTED 5 /* a combination this build does not implement  */
 #define RQR_ERR_HANDLE 6      /* NULL or destroyed handle                      */
+#define RQR_ERR_SIZE 7        /* problem larger than a fixed internal buffer   */
 
 /* Creates a handle bound to the current CUDA device and to `stream`
  * (a cudaStream_t; NULL = legacy default stream). (host) h receives the handle.
@@ -114,6 +115,24 @@ int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, in
  * Q (device, out) m x ncols, ld ldq; prec RQR_FP64 or RQR_FP32. */
 int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt,
                void* Q, int ldq, int ncols, int prec, void* work, size_t lwork);
+
+/* rqr_form_q without a workspace argument, for callers that cannot allocate
+ * device memory: code that must not call cudaMalloc (for example while a CUDA
+ * graph is being captured), real-time or signal-safe paths, and plug-ins whose
+ * host application owns every allocation and passes in only the input and
+ * output buffers. The paper has no counterpart; it is a deployment aid.
+ * Arguments and result are those of rqr_form_q without work/lwork. The
+ * scratch is one static device array of RQR_FORM_Q_NOALLOC_MAX_BYTES in the
+ * library, present on every GPU that loads it until the process exits; a
+ * problem whose scratch (m*b + 2*b*ncols values, plus some for partial sums)
+ * does not fit returns RQR_ERR_SIZE and queues nothing. The call allocates
+ * nothing. All calls share the array: calls whose GPU work overlaps (other
+ * streams or handles on the same device) race on it. The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. */
+#define RQR_FORM_Q_NOALLOC_MAX_BYTES (8u << 20)
+int rqr_form_q_noalloc(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt,
+                       void* Q, int ldq, int ncols, int prec);
 
 /* The dense products of the method, exposed for reuse and testing:
  * C = alpha op(A) op(B) + beta C (column-major, op = transpose when ta / tb is

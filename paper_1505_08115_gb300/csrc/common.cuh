@@ -154,6 +154,9 @@ void r_transpose(const Ctx& c, int kk, int cols, const T* F, int ldf, T* M, int 
 template <typename T>
 void copy_lower(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
 
+// Context of a live handle (false for a NULL or destroyed handle).
+bool handle_ctx(rqr_handle_t h, Ctx* out);
+
 }  // namespace rqr
 
 #define RQR_CUDA_TRY(x)                                  \

@@ -442,6 +442,15 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
 
 }  // namespace
 
+namespace rqr {
+// Stream, SM count, status word and launch counter of a live handle.
+bool handle_ctx(rqr_handle_t h, Ctx* out) {
+  if (!valid(h) || !out) return false;
+  *out = make_ctx(h);
+  return true;
+}
+}  // namespace rqr
+
 extern "C" {
 
 int rqr_create(rqr_handle_t* h, void* stream) {

@@ -23,11 +23,13 @@ SO_PATH = os.path.join(_HERE, "librqr.so")
 FP64, FP32, FP64X = 0, 1, 2
 SKETCH_DOWNDATE, SKETCH_RESAMPLE = 0, 1
 STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 4: "workspace too small",
-          5: "unsupported combination", 6: "invalid handle"}
+          5: "unsupported combination", 6: "invalid handle", 7: "problem larger than the fixed internal buffer"}
+FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 
 # every symbol declared in include/rqr.h
 EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_workspace_bytes", "rqrcp_factor", "rurv_factor",
-           "rqr_form_q", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill", "rqr_philox_raw",
+           "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill",
+           "rqr_philox_raw",
            "rqr_profile_enable", "rqr_profile_read", "rqr_version")
 PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final", "right")
 
@@ -59,6 +61,7 @@ def load(path: str = SO_PATH):
         L.rqrcp_factor.argtypes = [vp, i, i, vp, i, i, i, u64, vp, i, vp, i, vp, i, i, vp, sz, ip]
         L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, i, vp, sz, ip]
         L.rqr_form_q.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i, vp, sz]
+        L.rqr_form_q_noalloc.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i]
         L.rqr_gemm.argtypes = [vp, i, i, i, i, i, i, ctypes.c_double, vp, i, vp, i, ctypes.c_double, vp, i, vp, sz]
         L.rqr_gemm_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(sz)]
         L.rqr_gauss_fill.argtypes = [vp, u64, u64, i64, vp, i]
