@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64x"],
+                    help="fp64: FP64 DMMA products; fp64x: FP64-accurate bf16 tensor-core products")
+    ap.add_argument("--no-verify", action="store_true", help="skip the accuracy probe (profiling runs)")
     ap.add_argument("--seed", type=int, default=1505)
     ap.add_argument("--cpu-blocks", type=int, default=2, help="blocks of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -145,7 +148,7 @@ def make_matrix(n, seed, device):
 
 def workload_config(a):
     return {"workload": f"rqrcp m=n={a.n} b={a.b} p={a.p} sketch={a.sketch}, A = U diag(exp(-i/800)) V^T",
-            "m": a.n, "n": a.n, "b": a.b, "p": a.p, "sketch": a.sketch, "precision": "fp64",
+            "m": a.n, "n": a.n, "b": a.b, "p": a.p, "sketch": a.sketch, "precision": a.prec,
             "l2": "inputs larger than L2 (2 GiB matrix restored before every step)", "parallelism": "replicas"}
 
 
@@ -239,27 +242,33 @@ def main():
     A = rqr.empty_colmajor(n, n, torch.float64, dev)
     T = rqr.empty_colmajor(b, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64, sk), dtype=torch.uint8, device=dev)
+    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64X if a.prec == "fp64x" else rqr.FP64, sk),
+                       dtype=torch.uint8, device=dev)
     seed = a.seed + 1 + rank
     stream = torch.cuda.current_stream(dev)
 
+    emu = a.prec == "fp64x"
+
     def step():
-        rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False)
+        rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False, emulated=emu)
 
     for _ in range(a.warmup):
         A.copy_(A0)
         step()
     torch.cuda.synchronize()
-    # accuracy of the last warm-up result (random probes; the CPU cannot form Q at this size)
-    T_, perm_, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work)
-    g = torch.Generator(device=dev).manual_seed(7)
-    X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
-    R = torch.triu(A)
-    APx = A0[:, perm.long()] @ X
-    res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
-    orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
-            / torch.linalg.norm(X)).item()
-    del R, APx
+    res = orth = info = None
+    if not a.no_verify:
+        # accuracy of one factorization (random probes; the CPU cannot form Q at this size)
+        T_, perm_, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work,
+                                           emulated=emu)
+        g = torch.Generator(device=dev).manual_seed(7)
+        X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
+        R = torch.triu(A)
+        APx = A0[:, perm.long()] @ X
+        res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
+        orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
+                / torch.linalg.norm(X)).item()
+        del R, APx
 
     clocks = Clocks(device_index_for_smi(local_rank))
     if dist:

@@ -90,6 +90,13 @@ void set_mat(const Ctx& c, int r, int cols, T val, T* dst, int ldd);
 template <typename T>
 void make_vx(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv);
 
+// Strictly lower part of the factored panel (V without its unit diagonal).
+template <typename T>
+void make_vlow(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv);
+// dst += alpha * src (r x cols).
+template <typename T>
+void add_mat(const Ctx& c, int r, int cols, T alpha, const T* src, int lds, T* dst, int ldd);
+
 // ---------------------------------------------------------------- panel QR
 struct PanelWork;
 template <typename T>

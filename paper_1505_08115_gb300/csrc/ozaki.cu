@@ -16,17 +16,18 @@
 // Digits are exact in bf16; every product d_p d_q <= 127^2 is exact, and over
 // a K chunk of 128 a group holds at most 8 pairs: |S_g| <= 8*128*127^2 < 2^24,
 // so the tensor core's FP32 accumulation of a group is exact. After each
-// chunk the eight group sums are added into an FP64 accumulator with their
-// power-of-two scales; the dropped pairs (p+q >= 10) and digits (below 2^-56
-// of the row/column maximum) are far below FP64 rounding for the norm-wise
-// error of the product.
+// chunk the eight group sums are added exactly into two 64-bit integer
+// accumulators (shifted by their relative scales), converted to FP64 once at
+// the end; the dropped pairs (p+q >= 10) and digits (below 2^-56 of the
+// row/column maximum) are far below FP64 rounding for the norm-wise error of
+// the product.
 //
 // Kernel. CTA tile 64 x 32, eight warps of 16 x 16, K staged 32 at a time:
 // the FP64 tiles are loaded, split into digits and stored as bf16 slices
 // (k contiguous, rows padded to 40 for conflict-free fragment loads); each warp
 // keeps its eight A-slice fragments in registers and runs the 36 pairs x 2
 // n8 tiles = 72 mma.sync.m16n8k16 per k16 step into eight FP32 group
-// accumulators; the FP64 accumulator lives in shared memory.
+// accumulators; the integer accumulators live in shared memory.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -111,14 +112,15 @@ __global__ void __launch_bounds__(OT, 2) k_ozgemm(int M, int N, int K, int kchun
   extern __shared__ __align__(16) unsigned char smem[];
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);          // [ONS][OBM][OKP]
   __nv_bfloat16* Bs = As + ONS * OBM * OKP;                             // [ONS][OBN][OKP]
-  double* acc = reinterpret_cast<double*>(Bs + ONS * OBN * OKP);        // [OBN][OBM]
+  long long* accH = reinterpret_cast<long long*>(Bs + ONS * OBN * OKP);  // [OBN][OBM]
+  long long* accL = accH + OBM * OBN;                                     // [OBN][OBM]
   __shared__ int sea[OBM], seb[OBN];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wm = warp & 3, wn = warp >> 2;
   const int m0 = blockIdx.x * OBM, n0 = blockIdx.y * OBN;
   const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  for (int e = tid; e < OBM * OBN; e += OT) acc[e] = 0.0;
+  for (int e = tid; e < OBM * OBN; e += OT) accH[e] = accL[e] = 0;
   if (tid < OBM) sea[tid] = (m0 + tid < M) ? ea[m0 + tid] : 0;
   if (tid < OBN) seb[tid] = (n0 + tid < N) ? eb[n0 + tid] : 0;
   float S[8][2][4];
@@ -196,20 +198,24 @@ __global__ void __launch_bounds__(OT, 2) k_ozgemm(int M, int N, int K, int kchun
     __syncthreads();
     kin += OBK;
     if (kin >= OKC || k0 + OBK >= ke) {
-      // flush the exact group sums into the FP64 accumulator: group index
-      // p+q here is (g_true - 2), scale 2^(-7 g_true)
+      // flush the exact group sums (integers below 2^24) into two 64-bit
+      // integer accumulators: H collects groups a = 0..3 (scale 2^(-7(a+2)))
+      // as sum S_a 2^(7(3-a)), L groups 4..7 as sum S_a 2^(7(7-a)); so
+      // H 2^-35 + L 2^-63 is the chunk's value, and no rounding happens before
+      // the final conversion
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int r = wm * 16 + g + (c >> 1) * 8;
           const int col = wn * 16 + h * 8 + 2 * t + (c & 1);
-          // group a holds digit pairs with p + q = a + 2: scale 2^(-7(a+2))
-          const double sc[8] = {0x1p-14, 0x1p-21, 0x1p-28, 0x1p-35, 0x1p-42, 0x1p-49, 0x1p-56, 0x1p-63};
-          double s = 0.0;
+          long long hi = 0, lo = 0;
 #pragma unroll
-          for (int a = 7; a >= 0; --a) s = fma((double)S[a][h][c], sc[a], s);
-          acc[col * OBM + r] += s;
+          for (int a = 0; a < 4; ++a) hi += (long long)__float2int_rn(S[a][h][c]) << (7 * (3 - a));
+#pragma unroll
+          for (int a = 4; a < 8; ++a) lo += (long long)__float2int_rn(S[a][h][c]) << (7 * (7 - a));
+          accH[col * OBM + r] += hi;
+          accL[col * OBM + r] += lo;
 #pragma unroll
           for (int a = 0; a < 8; ++a) S[a][h][c] = 0.f;
         }
@@ -221,7 +227,8 @@ __global__ void __launch_bounds__(OT, 2) k_ozgemm(int M, int N, int K, int kchun
     const int r = e % OBM, col = e / OBM;
     const int i = m0 + r, j = n0 + col;
     if (i < M && j < N) {
-      const double v = ldexp(acc[col * OBM + r], sea[r] + seb[col]);
+      const double v =
+          ldexp(fma((double)accH[col * OBM + r], 0x1p-35, (double)accL[col * OBM + r] * 0x1p-63), sea[r] + seb[col]);
       if (part) {
         part[(size_t)blockIdx.z * M * N + i + (size_t)j * M] = v;
       } else {
@@ -244,7 +251,7 @@ __global__ void k_ozreduce(int M, int N, int S, double alpha, const double* __re
   }
 }
 
-constexpr size_t kOzSmem = sizeof(__nv_bfloat16) * ONS * (OBM + OBN) * OKP + sizeof(double) * OBM * OBN;
+constexpr size_t kOzSmem = sizeof(__nv_bfloat16) * ONS * (OBM + OBN) * OKP + 2 * sizeof(long long) * OBM * OBN;
 
 }  // namespace
 

@@ -451,6 +451,24 @@ __global__ void k_make_vx(int mp, int kb, const T* __restrict__ F, int ldf, T* _
   }
 }
 
+template <typename T>
+__global__ void k_make_vlow(int mp, int kb, const T* __restrict__ F, int ldf, T* __restrict__ V, int ldv) {
+  const int64_t n = (int64_t)mp * kb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % mp), j = (int)(e / mp);
+    V[i + (int64_t)j * ldv] = i > j ? F[i + (int64_t)j * ldf] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_add_mat(int r, int cols, T alpha, const T* __restrict__ s, int lds, T* d, int ldd) {
+  const int64_t n = (int64_t)r * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % r, j = e / r;
+    d[i + j * ldd] += alpha * s[i + j * lds];
+  }
+}
+
 int grid1d(int64_t n, int sms) {
   int64_t g = (n + 255) / 256;
   g = std::min<int64_t>(g, (int64_t)sms * 16);
@@ -577,7 +595,23 @@ void make_vx(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv) {
   note_launch(c);
 }
 
+template <typename T>
+void make_vlow(const Ctx& c, int mp, int kb, const T* F, int ldf, T* V, int ldv) {
+  if (mp <= 0 || kb <= 0) return;
+  k_make_vlow<T><<<grid1d((int64_t)mp * kb, c.sms), 256, 0, c.stream>>>(mp, kb, F, ldf, V, ldv);
+  note_launch(c);
+}
+
+template <typename T>
+void add_mat(const Ctx& c, int r, int cols, T alpha, const T* src, int lds, T* dst, int ldd) {
+  if (r <= 0 || cols <= 0) return;
+  k_add_mat<T><<<grid1d((int64_t)r * cols, c.sms), 256, 0, c.stream>>>(r, cols, alpha, src, lds, dst, ldd);
+  note_launch(c);
+}
+
 #define RQR_INST(T)                                                                                      \
+  template void make_vlow<T>(const Ctx&, int, int, const T*, int, T*, int);                               \
+  template void add_mat<T>(const Ctx&, int, int, T, const T*, int, T*, int);                              \
   template size_t panel_scratch_elems<T>(int, int, int);                                                \
   template void panel_qr<T>(const Ctx&, int, int, T*, int, T*, T*);                                       \
   template void qrcp_block<T>(const Ctx&, int, int, int, int, T*, int, int32_t*, T*, T*);                 \

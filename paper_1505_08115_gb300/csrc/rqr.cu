@@ -202,7 +202,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_FINAL, 2.0 * mp * np * (double)np - 2.0 * np * (double)np * np / 3.0);
       qrcp_block<T>(c, m, k0, k0, np, A, lda, perm, w.tau, w.pscr);
       make_vx<T>(c, mp, np, P, lda, w.Vx, mp);
-      mm(true, false, np, np, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, np);
+      gemm<T>(c, true, false, np, np, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, np, w.part, w.part_cap);
       larft_tri<T>(c, np, w.gram, np, w.tau, Tb, ldt);
       break;
     }
@@ -227,31 +227,52 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_SWAP, 0.0);
       apply_swaps<T>(c, b, w.picks, m, A, lda, k0, l, down ? w.Y : nullptr, l, k0, perm, w.swp, w.imap);
     }
-    // (d) panel QR + T
+    // (d) panel QR + T (the Gram matrix V^T V always in native precision)
     {
       Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)b * b - 2.0 * b * (double)b * b / 3.0);
       panel_qr<T>(c, mp, b, P, lda, w.tau, w.pscr);
       make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
-      mm(true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b);
+      gemm<T>(c, true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b, w.part, w.part_cap);
       larft_tri<T>(c, b, w.gram, b, w.tau, Tb, ldt);
     }
-    // (e) trailing update
+    // (e) trailing update. With the tensor-core products (emu) V is split into
+    // its unit diagonal E and strictly lower part L, V = E + L: the products
+    // with L keep full precision under per-row/column scaling (the unit entry
+    // would otherwise set the scale of every column of V), and the E parts are
+    // exact row/column additions.
     const int n2 = np - b;
     T* A2 = A + k0 + (size_t)(k0 + b) * lda;
+    if (emu) make_vlow<T>(c, mp, b, P, lda, w.Vx, mp);
     {
       Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * b);
-      mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(0), w.W, b);
-      mm(true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b);
-      mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);
+      if (!emu) {
+        mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(0), w.W, b);
+        gemm<T>(c, true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b, w.part, w.part_cap);
+        mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);
+      } else {
+        copy_mat<T>(c, b, n2, A2, lda, w.W, b);                              // E^T A2
+        mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(1), w.W, b);   // + L^T A2
+        gemm<T>(c, true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b, w.part, w.part_cap);
+        mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);  // - L W2
+        add_mat<T>(c, b, n2, T(-1), w.W2, b, A2, lda);                         // - E W2
+      }
     }
     if (down) {
       Phase ph(h, RQR_PHASE_DOWNDATE, 4.0 * l * mp * (double)b + 2.0 * l * b * (double)n2);
       T* Gk = w.Gc + (size_t)k0 * l;
-      mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(0), w.GV, l);
-      mm(false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l);
-      mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);
+      if (!emu) {
+        mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(0), w.GV, l);
+        gemm<T>(c, false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l, w.part, w.part_cap);
+        mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);
+      } else {
+        copy_mat<T>(c, l, b, Gk, l, w.GV, l);                                  // G E
+        mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(1), w.GV, l);      // + G L
+        gemm<T>(c, false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l, w.part, w.part_cap);
+        mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);     // - GVT L^T
+        add_mat<T>(c, l, b, T(-1), w.GVT, l, Gk, l);                           // - GVT E^T
+      }
       mm(false, false, l, n2, b, T(-1), Gk, l, A + k0 + (size_t)(k0 + b) * lda, lda, T(1),
-              w.Y + (size_t)(k0 + b) * l, l);
+         w.Y + (size_t)(k0 + b) * l, l);
     }
     k0 += b;
     ++blk;
