@@ -8,6 +8,12 @@ exp(-i/800), m = n = 16384, b = 128, p = 8, through the C ABI. A is restored
 from a resident copy before every step, outside the timed interval; every
 step touches 2 GiB, far more than the 129 MB L2, so no flush is needed.
 
+The headline mode is FP64X (FP64 data, FP64 panel/pivot/T steps, the large
+products as exact bf16 digit splittings on the tensor cores); the same
+workload on the native FP64 GPU path is timed in the same run and reported as
+"fp64_gpu" with the speedup (the metric compares against the FP64 GPU path at
+a fixed residual; both residuals are printed).
+
 Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (each
 rank factors its own matrix): value = all ranks' flops / max rank time.
 `--impl reference` times the CPU oracle instead, on a bounded sample (the
@@ -40,8 +46,9 @@ def parse():
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64x"],
+    ap.add_argument("--prec", default="fp64x", choices=["fp64", "fp64x"],
                     help="fp64: FP64 DMMA products; fp64x: FP64-accurate bf16 tensor-core products")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the native FP64 path")
     ap.add_argument("--no-verify", action="store_true", help="skip the accuracy probe (profiling runs)")
     ap.add_argument("--seed", type=int, default=1505)
     ap.add_argument("--cpu-blocks", type=int, default=2, help="blocks of the CPU-baseline sample")
@@ -242,81 +249,108 @@ def main():
     A = rqr.empty_colmajor(n, n, torch.float64, dev)
     T = rqr.empty_colmajor(b, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64X if a.prec == "fp64x" else rqr.FP64, sk),
-                       dtype=torch.uint8, device=dev)
+    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64X, sk), dtype=torch.uint8, device=dev)
     seed = a.seed + 1 + rank
     stream = torch.cuda.current_stream(dev)
-
-    emu = a.prec == "fp64x"
-
-    def step():
-        rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False, emulated=emu)
-
-    for _ in range(a.warmup):
-        A.copy_(A0)
-        step()
-    torch.cuda.synchronize()
-    res = orth = info = None
-    if not a.no_verify:
-        # accuracy of one factorization (random probes; the CPU cannot form Q at this size)
-        T_, perm_, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work,
-                                           emulated=emu)
-        g = torch.Generator(device=dev).manual_seed(7)
-        X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
-        R = torch.triu(A)
-        APx = A0[:, perm.long()] @ X
-        res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
-        orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
-                / torch.linalg.norm(X)).item()
-        del R, APx
-
-    clocks = Clocks(device_index_for_smi(local_rank))
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    rqr.profile_enable(True)
-    evs = []
-    for _ in range(a.steps):
-        A.copy_(A0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ck = clocks.stop()
-    prof = rqr.profile_read()
-    rqr.profile_enable(False)
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
     fl = rqrcp_flops(n, n, b, p, resample=(sk == rqr.SKETCH_RESAMPLE))
+
+    def measure(prec):
+        """W untimed + K timed factorizations in one precision mode."""
+        emu = prec == "fp64x"
+
+        def step():
+            rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False, emulated=emu)
+
+        for _ in range(a.warmup):
+            A.copy_(A0)
+            step()
+        torch.cuda.synchronize()
+        res = orth = info = None
+        if not a.no_verify:
+            # accuracy of one factorization (random probes; the CPU cannot form Q at this size)
+            _, _, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work,
+                                          emulated=emu)
+            g = torch.Generator(device=dev).manual_seed(7)
+            X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
+            R = torch.triu(A)
+            APx = A0[:, perm.long()] @ X
+            res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
+            orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
+                    / torch.linalg.norm(X)).item()
+            del R, APx
+        clocks = Clocks(device_index_for_smi(local_rank))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        rqr.profile_enable(True)
+        evs = []
+        for _ in range(a.steps):
+            A.copy_(A0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ck = clocks.stop()
+        prof = rqr.profile_read()
+        rqr.profile_enable(False)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return {"ms": ms, "prof": prof, "residual": res, "orthogonality": orth, "info": info, "clocks": ck,
+                "step": step}
+
+    head = measure(a.prec)
+    ms, prof = head["ms"], head["prof"]
     value = world * fl["total"] / (ms / 1e3) / 1e9
     launches = sum(v["launches"] for v in prof.values())
 
-    # roofline of the dominant kernel: the FP64 DMMA GEMMs of the trailing update
+    # roofline of the dominant kernel: the products of the trailing update
     pk, src = peaks()
-    peak64 = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
     up = prof["update"]
-    achieved = up["flops"] / (up["ms"] / 1e3) / 1e12 if up["ms"] > 0 else 0.0
-    roof = {"kernel": "trailing update (k_dgemm, mma.sync.m8n8k4.f64)", "bound": "tensor",
-            "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
-            "peak_source": f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 ratio 1.25/2250",
-            "traffic": None}
+    fp64_eq = up["flops"] / (up["ms"] / 1e3) / 1e12 if up["ms"] > 0 else 0.0
+    if a.prec == "fp64x":
+        # 36 bf16 digit-pair products per FP64 product (8 digits, pairs p + q <= 9)
+        achieved = 36.0 * fp64_eq
+        peak = pk["bf16_tflops"]
+        roof = {"kernel": "trailing update (k_ozgemm, mma.sync.m16n8k16 bf16, exact int64 accumulation)",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{src} bf16 dense {peak} TF/s (burst)", "fp64_equivalent_tflops": fp64_eq,
+                "traffic": None}
+    else:
+        peak = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+        roof = {"kernel": "trailing update (k_dgemm, mma.sync.m8n8k4.f64)", "bound": "tensor",
+                "achieved": fp64_eq, "peak": peak, "unit": "TFLOP/s", "frac": fp64_eq / peak,
+                "peak_source": f"{src} bf16 {pk['bf16_tflops']} TF/s x nominal FP64/bf16 ratio 1.25/2250",
+                "traffic": None}
 
+    cfg = workload_config(a)
+    cfg["precision"] = ("fp64x: FP64 data; panel, pivots, T in FP64; products as exact bf16 digit splittings "
+                        "(Ozaki scheme) on the tensor cores" if a.prec == "fp64x" else "fp64: FP64 DMMA products")
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "effective_gflops": world * conventional_qr_flops(n, n) / (ms / 1e3) / 1e9,
-           "residual": res, "orthogonality": orth, "device_status": info,
+           "residual": head["residual"], "orthogonality": head["orthogonality"], "device_status": head["info"],
            "phases": {k: {"ms": v["ms"] / a.steps, "gflops": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0,
                           "launches": v["launches"] // a.steps} for k, v in prof.items()},
-           "roofline": roof, "gpu_launches": launches, "clocks": ck}
+           "roofline": roof, "gpu_launches": launches, "clocks": head["clocks"]}
+    step = head["step"]
+
+    if a.prec != "fp64" and not a.no_fp64_compare:
+        # the same workload on the native FP64 GPU path, for "vs FP64 GPU"
+        base = measure("fp64")
+        out["fp64_gpu"] = {"ms_per_step": base["ms"], "value": world * fl["total"] / (base["ms"] / 1e3) / 1e9,
+                           "unit": "GFLOP/s", "residual": base["residual"], "orthogonality": base["orthogonality"],
+                           "update_tflops": base["prof"]["update"]["flops"] / (base["prof"]["update"]["ms"] / 1e3)
+                           / 1e12 if base["prof"]["update"]["ms"] else None, "clocks": base["clocks"]}
+        out["speedup_vs_fp64_gpu"] = base["ms"] / ms
 
     if not a.no_e2e:
         # end to end through the same C-ABI call with host buffers: pinned H2D of A,

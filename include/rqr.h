@@ -48,6 +48,7 @@ typedef struct rqr_handle_s* rqr_handle_t;
 #define RQR_OK 0
 #define RQR_ERR_CUDA 1        /* a CUDA call failed; the handle stays usable   */
 #define RQR_ERR_NONFINITE 2   /* a NaN/Inf reached a panel norm               */
+#define RQR_ERR_TIMEOUT 3     /* a bounded wait inside a kernel ran out       */
 #define RQR_ERR_WORKSPACE 4   /* lwork smaller than rqr_workspace_bytes        */
 #define RQR_ERR_UNSUPPORTED 5 /* a combination this build does not implement  */
 #define RQR_ERR_HANDLE 6      /* NULL or destroyed handle                      */

@@ -117,6 +117,11 @@ size_t panel_scratch_elems(int mp, int nc, int sms);
 template <typename T>
 void panel_qr(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch);
 
+// The same panel QR as one cooperative launch (persist.cu); false when the
+// panel does not fit (nothing queued). C, R: CTAs and rows per CTA.
+template <typename T>
+bool panel_qr_persist(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch, int C, int R);
+
 // Classical pivoted QR (Fig. QR) of rows r0..m-1, columns c0..c0+nc-1 of the
 // m x * matrix A; swaps move all m rows and perm[c0..].
 template <typename T>
@@ -135,6 +140,12 @@ size_t ypick_scratch_elems(int l, int np, int b, int sms);
 // picked positions (sequential-swap semantics) to picks[bsteps].
 template <typename T>
 void ypick(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy, int* picks, T* scratch);
+
+// The same b pivot steps as one cooperative launch with the sketch resident in
+// shared memory (persist.cu); false when it does not apply (nothing queued).
+size_t ypick_persist_scratch_bytes(int l, int np, int sms);
+template <typename T>
+bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy, int* picks, void* scratch);
 
 // Applies the swaps (j, picks[j]), j = 0..kb-1, in order to columns k0.. of
 // A (all m rows), to columns y0.. of Y (l rows, optional) and to perm[k0..].

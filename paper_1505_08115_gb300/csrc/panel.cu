@@ -18,111 +18,13 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "panel_common.cuh"
 
 namespace rqr {
 
 namespace {
 
-constexpr int PT = 256;        // threads per panel CTA
-constexpr int NCOEF = 4;       // tau, beta, d, has-reflector
-
-struct PanelArgs {
-  int mp, nc, R, ldp;
-};
-
-// Coefficients of the reflector of column j from its squared norm below the
-// diagonal (s_below) and its diagonal entry alpha (Sec. 3.1 with sign(0)=+1).
-template <typename T>
-__device__ void reflector_coef(int j, int mp, T alpha, T s_below, T* coef, T* tau_out, int* status) {
-  T tau = T(0), beta = alpha, d = T(1), has = T(0);
-  if (mp - j >= 2) {
-    has = T(1);
-    const T s = alpha * alpha + s_below;
-    if (!isfinite(s)) atomicCAS(status, 0, RQR_ERR_NONFINITE);
-    if (s == T(0)) {
-      beta = T(0);
-    } else {
-      const T nrm = sqrt(s);
-      beta = -sgn0(alpha) * nrm;
-      d = alpha - beta;
-      tau = (beta - alpha) / beta;
-    }
-  }
-  coef[0] = tau;
-  coef[1] = beta;
-  coef[2] = d;
-  coef[3] = has;
-  tau_out[j] = tau;
-}
-
-// Last-CTA step: totals of the partials for column jn (entry 0 = squared norm
-// below the diagonal, entry 1 + c = dot with column c) and its coefficients.
-// Lane l of every warp owns columns jn + l + 32k; warp w adds the partials of
-// CTAs w, w + 8, ... (independent loads, no long serial chain); the eight warp
-// sums are then added in warp order, so the result does not depend on timing.
-template <typename T>
-__device__ void finish_coef(int jn, const PanelArgs& a, const T* part, const T* rowbuf, T* coef, T* tau_out,
-                            int* status, T* red) {
-  constexpr int NW = PT / 32;
-  __shared__ T wred[NW][32 * 4];
-  const int C = gridDim.x, tid = threadIdx.x, nc = a.nc, lane = tid & 31, warp = tid >> 5;
-  for (int c0 = jn; c0 < nc; c0 += 32 * 4) {
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int q = warp; q < C; q += NW) {
-      const T* pq = part + (size_t)q * (nc + 1);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int c = c0 + lane + 32 * k;
-        if (c < nc) acc[k] += __ldcg(pq + (c == jn ? 0 : 1 + c));
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) wred[warp][lane + 32 * k] = acc[k];
-    __syncthreads();
-    for (int t = tid; t < 32 * 4; t += PT) {
-      const int c = c0 + t;
-      if (c < nc) {
-        T s = T(0);
-        for (int w = 0; w < NW; ++w) s += wred[w][t];
-        red[c] = s;
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0) reflector_coef<T>(jn, a.mp, __ldcg(rowbuf + jn), red[jn], coef, tau_out, status);
-  __syncthreads();
-  const T tau = coef[0], d = coef[2];
-  for (int c = jn + 1 + tid; c < nc; c += PT)
-    coef[NCOEF + c] = tau == T(0) ? T(0) : tau * (__ldcg(rowbuf + c) + red[c] / d);
-}
-
-// Ticket: returns true in exactly one CTA, the last one to get here, after all
-// other CTAs' global writes are visible to it.
-__device__ bool last_cta(int* counter) {
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int t = atomicAdd(counter, 1);
-    last = (t == (int)gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-template <typename T>
-__device__ T block_sum(T v, T* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  T s = T(0);
-  if (threadIdx.x == 0)
-    for (int i = 0; i < PT / 32; ++i) s += sh[i];
-  __syncthreads();
-  return s;  // valid in thread 0
-}
+using namespace pnl;
 
 // ------------------------------------------------------------ unpivoted panel
 template <typename T>
@@ -517,6 +419,8 @@ void panel_qr(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch) {
   if (mp <= 0 || nc <= 0) return;
   int C, R;
   panel_geometry(mp, nc, sizeof(T), c.sms, C, R);
+  // one cooperative launch with the panel resident in shared memory when it fits
+  if (panel_qr_persist<T>(c, mp, nc, P, ldp, tau, scratch, C, R)) return;
   T *part, *rowbuf, *coef;
   int *counter, *piv;
   carve_panel(scratch, C, nc, part, rowbuf, coef, counter, piv);

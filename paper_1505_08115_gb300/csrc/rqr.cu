@@ -92,6 +92,7 @@ template <typename T>
 struct RqrcpWs {
   T *Y, *Gc, *Vx, *W, *W2, *gram, *GV, *GVT, *tau, *part, *pscr, *yscr, *swp;
   int *picks, *imap, *iscr;
+  char* pers;
   size_t part_cap;
 };
 
@@ -137,6 +138,7 @@ size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs
   w.picks = cv.take<int>((size_t)b);
   w.imap = cv.take<int>(1 + 4 * (size_t)b + 8);
   w.iscr = cv.take<int>(rqr::ozaki_scratch_elems(std::max(m, l), std::max(n, m)));
+  w.pers = cv.take<char>(rqr::ypick_persist_scratch_bytes(l, std::max(n, 1), sms));
   return cv.used;
 }
 
@@ -221,7 +223,8 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
     // (b) pivots from the sketch, (c) swaps
     {
       Phase ph(h, RQR_PHASE_PIVOT, 4.0 * l * b * (double)np);
-      ypick<T>(c, l, np, b, w.Y + (size_t)k0 * l, l, w.picks, w.yscr);
+      if (!ypick_persist<T>(c, l, np, b, w.Y + (size_t)k0 * l, l, w.picks, w.pers))
+        ypick<T>(c, l, np, b, w.Y + (size_t)k0 * l, l, w.picks, w.yscr);
     }
     {
       Phase ph(h, RQR_PHASE_SWAP, 0.0);
