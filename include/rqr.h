@@ -138,9 +138,14 @@ int rqr_form_q_noalloc(rqr_handle_t h, int m, int n, int b, const void* F, int l
 /* The dense products of the method, exposed for reuse and testing:
  * C = alpha op(A) op(B) + beta C (column-major, op = transpose when ta / tb is
  * non-zero; A is M x K or K x M, B is K x N or N x K, all device memory).
- * prec RQR_FP64 (DMMA), RQR_FP32 (FFMA) or RQR_FP64X (bf16 tensor-core
- * splitting with FP64 accuracy); alpha, beta are converted to the precision.
- * work (device) of at least rqr_gemm_workspace_bytes bytes. */
+ * prec RQR_FP64 (DMMA), RQR_FP32 (FFMA) or RQR_FP64X (FP64 accuracy from bf16
+ * digit planes: 8 digits of 7 bits per value, 36 digit-pair products on the
+ * tcgen05 tensor cores with exact FP32 window sums, Ozaki et al. 2012);
+ * alpha, beta are converted to the precision. The FP64X error is bounded
+ * norm-wise: |error_ij| <~ K u max_k |a_ik| sum_k |b_kj| (u = 2^-53), like
+ * FP64's own product bound up to the row/column scaling.
+ * work (device) of at least rqr_gemm_workspace_bytes bytes (for FP64X it holds
+ * the digit planes of op(A) and of op(B): 16 bytes per element of each). */
 int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, double alpha, const void* A, int lda,
              const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork);
 int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes);
@@ -178,6 +183,12 @@ int rqr_profile_enable(rqr_handle_t h, int on);
  * count of the work queued in that phase, launches = kernels launched in it
  * (counted whether or not recording is on). Clears the counters. */
 int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches, int nphase);
+
+/* Waits for the handle's stream, then writes the summed CUDA-event time (ms),
+ * the algorithmic tensor-core flops (36 bf16 digit-pair products of 2 M N K
+ * each) and the launch count of the tcgen05 FP64X product kernel launched
+ * while tracing was on (host outputs, any may be NULL); clears them. */
+int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches);
 
 /* Library version string (static storage). */
 const char* rqr_version(void);

@@ -6,17 +6,50 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "../../include/rqr.h"
 
 namespace rqr {
 
 constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time too)
 
+// Event timing of one kernel class (the tcgen05 product kernel) while
+// profiling is on: CUDA events around each launch on the launch stream.
+struct KernelTimer {
+  int on = 0;
+  std::vector<cudaEvent_t> pool;  // 2 events per recorded launch
+  size_t used = 0;                // pairs recorded
+  double flops = 0.0;             // algorithmic tensor-core flops of the recorded launches
+  int64_t launches = 0;
+  // Records the start event of a launch; false when timing is off or an event cannot be made.
+  bool start(cudaStream_t s) {
+    if (!on) return false;
+    while (pool.size() < 2 * used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[2 * used], s);
+    return true;
+  }
+  void stop(cudaStream_t s, double fl) {
+    cudaEventRecord(pool[2 * used + 1], s);
+    ++used;
+    flops += fl;
+    ++launches;
+  }
+};
+
 struct Ctx {
   cudaStream_t stream;
   int sms;             // multiprocessor count of the device
   int* status;         // device status word (RQR_ERR_* or 0)
   int64_t* nlaunch;    // host-side count of kernel launches (may be null)
+  KernelTimer* kt = nullptr;  // optional per-launch timing of the tcgen05 products
 };
 
 // Counts kernel launches issued through a context (tracing aid).
@@ -132,6 +165,11 @@ void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int3
 template <typename T>
 void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt);
 
+// Gram matrix of V = E + L (unit diagonal E, strictly lower L, ld ldl) from
+// gram = L^T L on entry: adds I + L1 + L1^T (L1 = top kb x kb block of L).
+template <typename T>
+void gram_from_lower(const Ctx& c, int kb, const T* L, int ldl, T* gram, int ldg);
+
 // ---------------------------------------------------------------- sketch pivots
 template <typename T>
 size_t ypick_scratch_elems(int l, int np, int b, int sms);
@@ -158,6 +196,22 @@ void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, i
 size_t ozaki_scratch_elems(int M, int N);
 void gemm_f64x(const Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
                const double* B, int ldb, double beta, double* C, int ldc, int* iscr, double* part, size_t part_cap);
+
+// The same products on the tcgen05 tensor cores with TMA-staged digit planes
+// (oztc.cu). Returns false, with nothing queued, when the tensor-map encoder is
+// unavailable or the op(A) planes do not fit (the caller then falls back).
+struct TcScratch {
+  int* emax;      // M + N ints
+  uint16_t* pa;   // digit planes of op(A): pa_cap bf16
+  size_t pa_cap;
+  uint16_t* pb;   // digit planes of a column chunk of op(B): pb_cap bf16
+  size_t pb_cap;
+};
+size_t oztc_plane_elems(int rows, int K);
+bool oztc_available();
+bool gemm_f64x_tc(const Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
+                  const double* B, int ldb, double beta, double* C, int ldc, int* emax, uint16_t* pa, size_t pa_cap,
+                  uint16_t* pb, size_t pb_cap, double* part, size_t part_cap);
 
 // ---------------------------------------------------------------- small SVD
 // One-sided Jacobi on the r x cols matrix M (FP64, overwritten by M J); Js

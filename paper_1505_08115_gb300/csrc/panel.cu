@@ -294,12 +294,15 @@ __global__ void __launch_bounds__(PT) k_qrcp_apply(int j, int nsteps, PanelArgs 
 
 // ------------------------------------------------------------ T factor
 // T(0:j, j) = -tau_j T(0:j, 0:j) (V^T V)(0:j, j), T(j, j) = tau_j (Sec. 5.1),
-// one CTA, T kept in shared memory (kb <= 128) or global memory.
+// one CTA. T lives in shared memory when it fits (kb <= 160 in FP64), the
+// Gram column of the current step is staged in shared memory, and two threads
+// share each row's dot product (two independent accumulation chains).
 template <typename T>
 __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__ gram, int ldg, const T* tau, T* Tm,
                                                    int ldt, int use_smem) {
-  extern __shared__ unsigned char smem_raw[];
-  T* St = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* gcol = reinterpret_cast<T*>(smem_raw);  // [kb]
+  T* St = gcol + kb;
   const int tid = threadIdx.x;
   T* W = use_smem ? St : Tm;
   const int ldw = use_smem ? kb : ldt;
@@ -307,13 +310,25 @@ __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__
     const int i = e % kb, c = e / kb;
     W[i + (size_t)c * ldw] = T(0);
   }
-  __syncthreads();
   for (int j = 0; j < kb; ++j) {
+    for (int r = tid; r < j; r += blockDim.x) gcol[r] = gram[r + (size_t)j * ldg];
+    __syncthreads();
     const T tj = tau[j];
-    for (int i = tid; i < j; i += blockDim.x) {
-      T s = T(0);
-      for (int l = i; l < j; ++l) s += W[i + (size_t)l * ldw] * gram[l + (size_t)j * ldg];
-      W[i + (size_t)j * ldw] = -tj * s;
+    // rows i = pair index, two threads per row (adjacent lanes) split l
+    for (int base = 0; base < j; base += (int)blockDim.x / 2) {
+      const int i = base + (tid >> 1), h = tid & 1;
+      T s0 = T(0), s1 = T(0);
+      if (i < j) {
+        int l = i + h;
+        for (; l + 2 < j; l += 4) {
+          s0 += W[i + (size_t)l * ldw] * gcol[l];
+          s1 += W[i + (size_t)(l + 2) * ldw] * gcol[l + 2];
+        }
+        if (l < j) s0 += W[i + (size_t)l * ldw] * gcol[l];
+      }
+      T s = s0 + s1;
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (i < j && h == 0) W[i + (size_t)j * ldw] = -tj * s;
     }
     if (tid == 0) W[j + (size_t)j * ldw] = tj;
     __syncthreads();
@@ -323,6 +338,17 @@ __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__
       const int i = e % kb, c = e / kb;
       Tm[i + (size_t)c * ldt] = St[i + (size_t)c * kb];
     }
+}
+
+// Gram matrix of V = E + L from the Gram matrix of its strictly lower part:
+// V^T V = L^T L + I + L1 + L1^T, L1 = the top kb x kb block of L.
+template <typename T>
+__global__ void k_gram_from_lower(int kb, const T* __restrict__ L, int ldl, T* gram, int ldg) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kb * kb; e += gridDim.x * blockDim.x) {
+    const int i = e % kb, j = e / kb;
+    T add = i == j ? T(1) : (i > j ? L[i + (size_t)j * ldl] : L[j + (size_t)i * ldl]);
+    gram[i + (size_t)j * ldg] += add;
+  }
 }
 
 // ------------------------------------------------------------ helpers
@@ -470,13 +496,22 @@ void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int3
 template <typename T>
 void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt) {
   if (kb <= 0) return;
-  const size_t need = sizeof(T) * (size_t)kb * kb;
+  const size_t need = sizeof(T) * ((size_t)kb * kb + kb);
   const int use_smem = need <= 200 * 1024 ? 1 : 0;
-  const size_t sm = use_smem ? need : 0;
+  const size_t sm = use_smem ? need : sizeof(T) * (size_t)kb;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_larft_tri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_larft_tri<T><<<1, 256, sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt, use_smem);
   note_launch(c);
 }
+
+template <typename T>
+void gram_from_lower(const Ctx& c, int kb, const T* L, int ldl, T* gram, int ldg) {
+  if (kb <= 0) return;
+  k_gram_from_lower<T><<<ceil_div(kb * kb, 256), 256, 0, c.stream>>>(kb, L, ldl, gram, ldg);
+  note_launch(c);
+}
+template void gram_from_lower<double>(const Ctx&, int, const double*, int, double*, int);
+template void gram_from_lower<float>(const Ctx&, int, const float*, int, float*, int);
 
 template <typename T>
 void copy_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd) {

@@ -35,7 +35,7 @@ __device__ __forceinline__ void reflector_coef(int j, int mp, T alpha, T s_below
   coef[1] = beta;
   coef[2] = d;
   coef[3] = has;
-  tau_out[j] = tau;
+  if (tau_out) tau_out[j] = tau;
 }
 
 // Last-CTA step: totals of the partials for column jn (entry 0 = squared norm

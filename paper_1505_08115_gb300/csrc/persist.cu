@@ -1,17 +1,18 @@
-// persist.cu -- the b pivot steps of the sketch (Sec. 4.1 with the
-// over-sampling of Sec. 4.3: first b steps of Fig. QR on the l x n' sketch) as
-// ONE cooperative launch instead of one launch per step.
+// persist.cu -- the two latency-bound steps of every block as single
+// cooperative launches: the b pivot steps on the sketch (Sec. 4.1 with the
+// over-sampling of Sec. 4.3: first b steps of Fig. QR on the l x n' sketch)
+// and the Householder QR of the m' x b panel (Sec. 3.2).
 //
-// Every CTA keeps the sketch columns of its fixed range of positions resident
-// in shared memory for all b steps (l x ~108 FP64 values per SM at n' = 16384),
-// so a step reads no global memory except the reflector and the column that
-// the swap brings in. Steps are separated by a grid barrier: the last CTA to
-// arrive picks the largest remaining norm (lowest position on ties), builds
-// the next reflector from the candidate column the winning CTA published, and
-// releases the others. Waiting CTAs spin with a bounded count; a wait that
-// runs out sets RQR_ERR_TIMEOUT in the status word and every CTA returns at
-// the next barrier (co-residency is guaranteed by the cooperative launch, so
-// this only guards against a defect).
+// Each CTA keeps its slice resident in shared memory for all steps (sketch
+// columns of a fixed range of positions; panel rows of a fixed range), so a
+// step reads no global memory except the few values the CTAs exchange. Steps
+// are separated by an arrival barrier on a counter that only grows (one
+// device-scope atomic per CTA, no release phase), and the data exchanged
+// through global memory is reduced by every CTA (pivot winner) or by one CTA
+// per entry (panel sums) in a fixed order, so results do not depend on timing.
+// Waits are bounded by ~2 s of global time; a wait that runs out sets
+// RQR_ERR_TIMEOUT in the status word and every CTA returns (co-residency is
+// guaranteed by the cooperative launch, so this only guards against a defect).
 #include <algorithm>
 
 #include "common.cuh"
@@ -22,11 +23,12 @@ namespace rqr {
 namespace {
 
 constexpr int PT = 256, PNW = PT / 32;
-constexpr unsigned kMaxSpins = 1u << 24;  // x ~100 ns sleep: ~2 s
 
 struct GridSync {
-  unsigned count, gen;
-  int err, pad;
+  unsigned count;  // arrivals so far (zeroed before the launch)
+  unsigned pad0;
+  int err;         // set by a CTA whose wait ran out
+  int pad1;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -34,55 +36,36 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+
+// Arrival barrier on a counter that only grows: CTA arrivals of step s bring
+// it to C (s + 1). Thread 0 of every CTA publishes its CTA's writes with a
+// device-scope fence and one atomic, then spins (bounded by ~2 s of global
+// time) until every CTA has arrived; false when the wait ran out or another
+// CTA gave up.
+__device__ __forceinline__ uint64_t gtime_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// Arrive; returns true in the last CTA to arrive (the caller then does the
-// step's serial work and calls grid_release). Others wait for the release.
-__device__ bool grid_arrive(GridSync* gs, unsigned& gen_seen) {
-  __shared__ int s_last;
-  __shared__ unsigned s_gen;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire(&gs->gen);
-    __threadfence();
-    const unsigned t = atomicAdd(&gs->count, 1u);
-    s_last = (t == gridDim.x - 1) ? 1 : 0;
-    s_gen = g;
-  }
-  __syncthreads();
-  gen_seen = s_gen;
-  if (s_last) __threadfence();
-  return s_last != 0;
-}
-
-__device__ void grid_release(GridSync* gs, unsigned gen_seen) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    gs->count = 0;
-    __threadfence();
-    st_release(&gs->gen, gen_seen + 1);
-  }
-}
-
-// Waits for the release of generation gen_seen; false when the wait ran out
-// or another CTA reported one.
-__device__ bool grid_wait(GridSync* gs, unsigned gen_seen, int* status) {
+__device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* status) {
   __shared__ int s_ok;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned spins = 0;
+    __threadfence();
+    atomicAdd(count, 1u);
     int ok = 1;
-    while (ld_acquire(&gs->gen) == gen_seen) {
-      if (++spins > kMaxSpins || *(volatile int*)&gs->err) {
-        atomicExch(&gs->err, 1);
-        atomicCAS(status, 0, RQR_ERR_TIMEOUT);
-        ok = 0;
-        break;
+    if (ld_acquire(count) < target) {
+      const uint64_t t0 = gtime_ns();
+      while (ld_acquire(count) < target) {
+        if (*(volatile int*)err || gtime_ns() - t0 > 2000000000ull) {
+          atomicExch(err, 1);
+          atomicCAS(status, 0, RQR_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
-      __nanosleep(100);
     }
-    if (*(volatile int*)&gs->err) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
@@ -95,78 +78,36 @@ struct PArgs {
   const T* Y;
   int ldy;
   int* picks;
-  T* cand_n;
-  int* cand_p;
-  T* candcol;  // [C][l]
-  T* vbuf;     // [l + 2]
-  T* colbuf;   // [2][l]
+  T* cand_n;    // [2][C] candidate squared norms (step parity)
+  int* cand_p;  // [2][C] candidate positions
+  T* candcol;   // [2][C][l] candidate columns
+  T* colbuf;    // [2][l] column leaving the pivot position
   GridSync* gs;
   int* status;
 };
 
-// Last CTA: global best over the CTA candidates, pick, and the reflector of
-// rows j..l-1 of the winner's published column.
+// Better candidate: larger squared norm, lower position on ties.
 template <typename T>
-__device__ void reduce_pick(int j, const PArgs<T>& a) {
-  __shared__ T sn[PT];
-  __shared__ int sp[PT], sq[PT];
-  const int tid = threadIdx.x, lane = tid & 31;
-  T bn = T(-1);
-  int bp = 0x7fffffff, bq = 0;
-  for (int q = tid; q < (int)gridDim.x; q += PT) {
-    const T n = __ldcg(a.cand_n + q);
-    const int p = __ldcg(a.cand_p + q);
-    if (n > bn || (n == bn && p < bp)) {
-      bn = n;
-      bp = p;
-      bq = q;
-    }
-  }
-  sn[tid] = bn;
-  sp[tid] = bp;
-  sq[tid] = bq;
-  __syncthreads();
-  for (int half = PT / 2; half > 0; half >>= 1) {
-    if (tid < half && (sn[tid + half] > sn[tid] || (sn[tid + half] == sn[tid] && sp[tid + half] < sp[tid]))) {
-      sn[tid] = sn[tid + half];
-      sp[tid] = sp[tid + half];
-      sq[tid] = sq[tid + half];
-    }
-    __syncthreads();
-  }
-  if (tid < 32) {
-    const T* y = a.candcol + (size_t)sq[0] * a.l;
-    const int L = a.l - j;
-    T s = T(0);
-    for (int r = lane; r < L; r += 32) {
-      const T x = __ldcg(y + j + r);
-      s += x * x;
-    }
-    s = warp_sum(s);
-    const T alpha = __ldcg(y + j);
-    T tau = T(0), d = T(1);
-    if (L >= 2 && s > T(0)) {
-      const T beta = -sgn0(alpha) * sqrt(s);
-      d = alpha - beta;
-      tau = (beta - alpha) / beta;
-    }
-    for (int r = 1 + lane; r < L; r += 32) a.vbuf[1 + r] = tau == T(0) ? T(0) : __ldcg(y + j + r) / d;
-    if (lane == 0) {
-      a.vbuf[0] = tau;
-      a.vbuf[1] = T(1);
-      a.picks[j] = sp[0];
-    }
-  }
+__device__ __forceinline__ bool better(T n, int p, T bn, int bp) {
+  return n > bn || (n == bn && p < bp);
 }
 
+// b steps of Fig. QR on the sketch. Per step s every CTA publishes its best
+// remaining column (squared norm of rows s.., position, values), meets the
+// others at the arrival barrier, and then picks the global winner itself from
+// the C published candidates (same data and order in every CTA, so the same
+// winner), builds the reflector from the winner's values and applies it to its
+// own columns. One barrier per step and no serial phase in a single CTA.
 template <typename T>
 __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int l = a.l;
+  const int l = a.l, C = gridDim.x;
   T* tile = reinterpret_cast<T*>(smem_raw);  // [per][l]
   T* v = tile + (size_t)a.per * l;            // [l]
   __shared__ T shn[PNW];
-  __shared__ int shp[PNW];
+  __shared__ int shp[PNW], shq[PNW];
+  __shared__ T s_tau;
+  __shared__ int s_win, s_pos;
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lo = q * a.per, hi = min(a.np, lo + a.per), cnt = max(0, hi - lo);
   for (int e = tid; e < cnt * l; e += PT) {
@@ -174,22 +115,22 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     tile[e] = a.Y[(size_t)(lo + pl) * a.ldy + r];
   }
   __syncthreads();
-  // full column norms, CTA candidate
+  // full column norms, warp candidates
   T wn = T(-1);
   int wp = 0x7fffffff;
   for (int pl = warp; pl < cnt; pl += PNW) {
     const T* y = tile + (size_t)pl * l;
-    T s = T(0);
-    for (int r = lane; r < l; r += 32) s += y[r] * y[r];
-    s = warp_sum(s);
-    if (s > wn || (s == wn && lo + pl < wp)) {
-      wn = s;
+    T ss = T(0);
+    for (int r = lane; r < l; r += 32) ss += y[r] * y[r];
+    ss = warp_sum(ss);
+    if (better(ss, lo + pl, wn, wp)) {
+      wn = ss;
       wp = lo + pl;
     }
   }
-  int j = -1;
-  for (;;) {
-    // ---- publish this CTA's candidate (value, position, column rows j+1..)
+  for (int s = 0; s < a.bsteps; ++s) {
+    const int par = s & 1;
+    // ---- publish the CTA candidate and, if owned, the column at position s
     if (lane == 0) {
       shn[warp] = wn;
       shp[warp] = wp;
@@ -198,53 +139,111 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     T bn = T(-1);
     int bp = 0x7fffffff;
     for (int w = 0; w < PNW; ++w)
-      if (shn[w] > bn || (shn[w] == bn && shp[w] < bp)) {
+      if (better(shn[w], shp[w], bn, bp)) {
         bn = shn[w];
         bp = shp[w];
       }
     if (tid == 0) {
-      a.cand_n[q] = bn;
-      a.cand_p[q] = bp;
+      a.cand_n[par * C + q] = bn;
+      a.cand_p[par * C + q] = bp;
     }
     if (bp >= lo && bp < hi)
-      for (int r = j + 1 + tid; r < l; r += PT) a.candcol[(size_t)q * l + r] = tile[(size_t)(bp - lo) * l + r];
-    // the content of position j+1 moves to the next pivot's position: publish it
-    if (j + 2 < a.bsteps + 1 && j + 1 >= lo && j + 1 < hi)
-      for (int r = j + 1 + tid; r < l; r += PT)
-        a.colbuf[(size_t)((j + 1) & 1) * l + r] = tile[(size_t)(j + 1 - lo) * l + r];
-    unsigned gen;
-    if (grid_arrive(a.gs, gen)) {
-      reduce_pick<T>(j + 1, a);
-      grid_release(a.gs, gen);
-    } else if (!grid_wait(a.gs, gen, a.status)) {
-      return;
+      for (int r = s + tid; r < l; r += PT) a.candcol[((size_t)par * C + q) * l + r] = tile[(size_t)(bp - lo) * l + r];
+    if (s >= lo && s < hi)
+      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * l + r] = tile[(size_t)(s - lo) * l + r];
+    if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status)) return;
+    // ---- global winner (every CTA, identical order)
+    T cn = T(-1);
+    int cp = 0x7fffffff, cq = 0;
+    for (int t = tid; t < C; t += PT) {
+      const T n = __ldcg(a.cand_n + par * C + t);
+      const int pp = __ldcg(a.cand_p + par * C + t);
+      if (better(n, pp, cn, cp)) {
+        cn = n;
+        cp = pp;
+        cq = t;
+      }
     }
-    ++j;  // now step j: positions j and picks[j] swap, reflector j applies
-    if (j + 1 >= a.bsteps) break;
-    // ---- step j
-    const int pj = __ldcg(a.picks + j);
-    const int L = l - j;
-    for (int r = tid; r < L; r += PT) v[r] = __ldcg(a.vbuf + 1 + r);
-    const T tau = __ldcg(a.vbuf);
-    if (pj != j && pj >= lo && pj < hi)
-      for (int r = j + tid; r < l; r += PT) tile[(size_t)(pj - lo) * l + r] = __ldcg(a.colbuf + (size_t)(j & 1) * l + r);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T n2 = __shfl_xor_sync(0xffffffffu, cn, o);
+      const int p2 = __shfl_xor_sync(0xffffffffu, cp, o);
+      const int q2 = __shfl_xor_sync(0xffffffffu, cq, o);
+      if (better(n2, p2, cn, cp)) {
+        cn = n2;
+        cp = p2;
+        cq = q2;
+      }
+    }
+    if (lane == 0) {
+      shn[warp] = cn;
+      shp[warp] = cp;
+      shq[warp] = cq;
+    }
     __syncthreads();
+    if (tid == 0) {
+      T gn = shn[0];
+      int gp = shp[0], gq = shq[0];
+      for (int w = 1; w < PNW; ++w)
+        if (better(shn[w], shp[w], gn, gp)) {
+          gn = shn[w];
+          gp = shp[w];
+          gq = shq[w];
+        }
+      s_win = gq;
+      s_pos = gp;
+      if (q == 0) a.picks[s] = gp;
+    }
+    __syncthreads();
+    const int qj = s_win, pw = s_pos;  // winning CTA and position (the same in every CTA)
+    const T* ycol = a.candcol + ((size_t)par * C + qj) * l;
+    const int L = l - s;
+    if (warp == 0) {
+      // reflector of rows s.. of the winner (Sec. 3.1, sign(0) = +1)
+      T ss = T(0);
+      for (int r = lane; r < L; r += 32) {
+        const T x = __ldcg(ycol + s + r);
+        v[r] = x;
+        ss += x * x;
+      }
+      ss = warp_sum(ss);
+      const T alpha = __ldcg(ycol + s);
+      T tau = T(0), d = T(1);
+      if (L >= 2 && ss > T(0)) {
+        const T beta = -sgn0(alpha) * sqrt(ss);
+        d = alpha - beta;
+        tau = (beta - alpha) / beta;
+      }
+      __syncwarp();
+      for (int r = 1 + lane; r < L; r += 32) v[r] = tau == T(0) ? T(0) : v[r] / d;
+      if (lane == 0) {
+        v[0] = T(1);
+        s_tau = tau;
+      }
+    } else if (pw != s && pw >= lo && pw < hi) {
+      // the column that was at position s moves to the winner's position
+      for (int r = s + tid - 32; r < l; r += PT - 32) tile[(size_t)(pw - lo) * l + r] = __ldcg(a.colbuf + (size_t)par * l + r);
+    }
+    __syncthreads();
+    if (s + 1 >= a.bsteps) break;
+    // ---- apply the reflector to the remaining columns, norms of rows s+1..
+    const T tau = s_tau;
     wn = T(-1);
     wp = 0x7fffffff;
-    for (int pl = max(0, j + 1 - lo) + warp; pl < cnt; pl += PNW) {
-      T* y = tile + (size_t)pl * l + j;
+    for (int pl = max(0, s + 1 - lo) + warp; pl < cnt; pl += PNW) {
+      T* y = tile + (size_t)pl * l + s;
       T dot = T(0);
       for (int r = lane; r < L; r += 32) dot += v[r] * y[r];
       dot = warp_sum(dot) * tau;
-      T s = T(0);
+      T ss = T(0);
       for (int r = lane; r < L; r += 32) {
         const T nx = y[r] - dot * v[r];
         y[r] = nx;
-        if (r >= 1) s += nx * nx;
+        if (r >= 1) ss += nx * nx;
       }
-      s = warp_sum(s);
-      if (s > wn || (s == wn && lo + pl < wp)) {
-        wn = s;
+      ss = warp_sum(ss);
+      if (better(ss, lo + pl, wn, wp)) {
+        wn = ss;
         wp = lo + pl;
       }
     }
@@ -270,30 +269,74 @@ struct QArgs {
   int* status;
 };
 
+// Column totals of the CTA partials: CTA e adds entry e of all C partial
+// vectors (one load per thread, a fixed-order tree), so every total has the
+// same value whichever CTA computes or reads it.
+template <typename T>
+__device__ __forceinline__ void reduce_entry(int e, int nc, const T* part, T* total) {
+  __shared__ T wsum[pnl::PT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, C = gridDim.x;
+  T x = T(0);
+  for (int q = tid; q < C; q += pnl::PT) x += __ldcg(part + (size_t)q * (nc + 1) + e);
+  x = warp_sum(x);
+  if (lane == 0) wsum[warp] = x;
+  __syncthreads();
+  if (tid == 0) {
+    T t = T(0);
+    for (int w = 0; w < pnl::PT / 32; ++w) t += wsum[w];
+    total[e] = t;
+  }
+  __syncthreads();
+}
+
+// Householder QR of an mp x nc panel (Sec. 3.2) as one cooperative launch:
+// each CTA keeps its rows of all nc columns in shared memory for the whole
+// panel. Per column j: the CTAs update column j+1 and the columns after it and
+// publish partial sums (squared norm of column j+1 below the diagonal, its
+// dot products with the later columns); after an arrival barrier CTA e adds
+// entry e over all CTAs; after a second barrier every CTA reads the totals and
+// computes the next reflector's coefficients itself.
 template <typename T>
 __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   using namespace pnl;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nc = a.nc, R = a.R;
+  const int nc = a.nc, R = a.R, C = gridDim.x;
   T* w = reinterpret_cast<T*>(smem_raw);  // [nc]
   T* tile = w + nc;                       // [nc][R]: tile[c * R + rr] = P(r0 + rr, c)
   __shared__ T wsum[PT / 32];
+  __shared__ T s_coef[NCOEF];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
-  const PanelArgs pa{a.mp, nc, R, a.ldp};
+  T* total = a.coef;  // [nc + 1]
+  unsigned nbar = 0;
   for (int e = tid; e < nr * nc; e += PT) {
     const int rr = e % nr, cc = e / nr;
     tile[cc * R + rr] = a.P[r0 + rr + (size_t)cc * a.ldp];
   }
   __syncthreads();
+  // Exchange after the partials of column jn are published: totals, then the
+  // coefficients of jn's reflector and w[c] = tau (x_jn,c + dot_c / d), c > jn.
+  auto exchange = [&](int jn) -> bool {
+    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status)) return false;
+    for (int e = q; e <= nc; e += C)
+      if (e == 0 || e >= jn + 2) reduce_entry<T>(e, nc, a.part, total);
+    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status)) return false;
+    const T* rb = a.rowbuf + (size_t)(jn & 1) * nc;
+    if (tid == 0) reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
+    __syncthreads();
+    const T tau = s_coef[0], d = s_coef[2];
+    for (int c = tid; c < nc; c += PT) w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) / d) : T(0);
+    __syncthreads();
+    return true;
+  };
   // partials of column 0 (below the diagonal) and row 0
   {
     T* myp = a.part + (size_t)q * (nc + 1);
-    T s = T(0);
+    T ssum = T(0);
     for (int rr = tid; rr < nr; rr += PT)
-      if (r0 + rr > 0) s += tile[rr] * tile[rr];
-    s = block_sum(s, wsum);
-    if (tid == 0) myp[0] = s;
+      if (r0 + rr > 0) ssum += tile[rr] * tile[rr];
+    ssum = block_sum(ssum, wsum);
+    if (tid == 0) myp[0] = ssum;
     for (int c = 1 + warp; c < nc; c += PT / 32) {
       T acc = T(0);
       for (int rr = lane; rr < nr; rr += 32)
@@ -303,22 +346,13 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     }
     if (r0 == 0 && nr > 0)
       for (int c = tid; c < nc; c += PT) a.rowbuf[c] = tile[(size_t)c * R];
-    unsigned gen;
-    if (grid_arrive(a.gs, gen)) {
-      finish_coef<T>(0, pa, a.part, a.rowbuf, a.coef, a.tau, a.status, w);
-      grid_release(a.gs, gen);
-    } else if (!grid_wait(a.gs, gen, a.status)) {
-      return;
-    }
+    if (!exchange(0)) return;
   }
   for (int j = 0; j < nc; ++j) {
-    const T* cin = a.coef + (size_t)(j & 1) * (NCOEF + nc);
-    for (int c = tid; c < nc; c += PT) w[c] = c > j ? __ldcg(cin + NCOEF + c) : T(0);
-    const T tauj = __ldcg(cin), beta = __ldcg(cin + 1), d = __ldcg(cin + 2);
-    const bool has = __ldcg(cin + 3) != T(0);
+    const T tauj = s_coef[0], beta = s_coef[1], d = s_coef[2];
+    const bool has = s_coef[3] != T(0);
     const int lo = min(nr, max(0, j - r0));
     T* tj = tile + (size_t)j * R;
-    __syncthreads();
     for (int rr = lo + tid; rr < nr; rr += PT) {
       const int i = r0 + rr;
       if (i > j) {
@@ -337,11 +371,11 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     }
     __syncthreads();
     T* myp = a.part + (size_t)q * (nc + 1);
-    T s = T(0);
+    T ssum = T(0);
     for (int rr = lo + tid; rr < nr; rr += PT)
-      if (r0 + rr > j + 1) s += t1[rr] * t1[rr];
-    s = block_sum(s, wsum);
-    if (tid == 0) myp[0] = s;
+      if (r0 + rr > j + 1) ssum += t1[rr] * t1[rr];
+    ssum = block_sum(ssum, wsum);
+    if (tid == 0) myp[0] = ssum;
     for (int c = j + 2 + warp; c < nc; c += PT / 32) {
       T* x = tile + (size_t)c * R;
       const T wc = w[c];
@@ -355,17 +389,11 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       acc = warp_sum(acc);
       if (lane == 0) myp[1 + c] = acc;
     }
-    __syncthreads();
+    __syncthreads();  // row j+1 of every column is final before it is published
     T* rb = a.rowbuf + (size_t)((j + 1) & 1) * nc;
     if (j + 1 >= r0 && j + 1 < r1)
       for (int c = j + 1 + tid; c < nc; c += PT) rb[c] = tile[(size_t)c * R + (j + 1 - r0)];
-    unsigned gen;
-    if (grid_arrive(a.gs, gen)) {
-      finish_coef<T>(j + 1, pa, a.part, rb, a.coef + (size_t)((j + 1) & 1) * (NCOEF + nc), a.tau, a.status, w);
-      grid_release(a.gs, gen);
-    } else if (!grid_wait(a.gs, gen, a.status)) {
-      return;
-    }
+    if (!exchange(j + 1)) return;
   }
   __syncthreads();
   for (int e = tid; e < nr * nc; e += PT) {
@@ -427,7 +455,7 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
 size_t ypick_persist_scratch_bytes(int l, int np, int sms) {
   int C, per;
   persist_smem(l, np, sms, C, per);
-  return 64 + sizeof(double) * ((size_t)C * (l + 1) + 3 * (size_t)l + 16) + sizeof(int) * (size_t)C + 256;
+  return 64 + sizeof(double) * (2 * (size_t)C * (l + 1) + 2 * (size_t)l + 16) + sizeof(int) * 2 * (size_t)C + 256;
 }
 
 // Returns false (and queues nothing) when the sketch slice does not fit in
@@ -454,12 +482,11 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
   GridSync* gs = reinterpret_cast<GridSync*>(p);
   p += 64;
   T* cand_n = reinterpret_cast<T*>(p);
-  T* candcol = cand_n + C;
-  T* vbuf = candcol + (size_t)C * l;
-  T* colbuf = vbuf + l + 2;
+  T* candcol = cand_n + 2 * (size_t)C;
+  T* colbuf = candcol + 2 * (size_t)C * l;
   int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)l + 8);
   cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_n, cand_p, candcol, vbuf, colbuf, gs, c.status};
+  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_n, cand_p, candcol, colbuf, gs, c.status};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_ypick_persist<T>, dim3(C), dim3(PT), args, smem, c.stream) !=
       cudaSuccess) {

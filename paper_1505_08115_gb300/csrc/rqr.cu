@@ -42,6 +42,7 @@ struct rqr_handle_s {
   int* d_status;
   int64_t nlaunch;
   RqrProfile prof;
+  rqr::KernelTimer kt;
 };
 
 namespace {
@@ -50,7 +51,7 @@ constexpr unsigned kMagic = 0x52515231u;  // "RQR1"
 
 bool valid(rqr_handle_t h) { return h && h->magic == kMagic; }
 
-rqr::Ctx make_ctx(rqr_handle_t h) { return rqr::Ctx{h->stream, h->sms, h->d_status, &h->nlaunch}; }
+rqr::Ctx make_ctx(rqr_handle_t h) { return rqr::Ctx{h->stream, h->sms, h->d_status, &h->nlaunch, &h->kt}; }
 
 // Scope of one phase: start/end events when profiling is on, launches and
 // algorithmic flops attributed to the phase.
@@ -94,7 +95,30 @@ struct RqrcpWs {
   int *picks, *imap, *iscr;
   char* pers;
   size_t part_cap;
+  rqr::TcScratch tc;
 };
+
+// Scratch of the tcgen05 FP64-accurate products (FP64X mode): exponent maxima,
+// digit planes of op(A) and of op(B) (op(B) is split in column chunks that fit
+// into at most kTcPlaneBudget bf16 values).
+constexpr size_t kTcPlaneBudget = (size_t)512 << 20;
+
+void carve_tc(rqr::Carver& cv, size_t emax_elems, size_t pa_elems, size_t pb_elems, rqr::TcScratch& s) {
+  s.emax = cv.take<int>(emax_elems);
+  s.pa_cap = pa_elems;
+  s.pa = cv.take<uint16_t>(pa_elems);
+  s.pb_cap = pb_elems;
+  s.pb = cv.take<uint16_t>(pb_elems);
+}
+
+// Scratch of one FP64X product through rqr_gemm.
+void gemm_tc_carve(rqr::Carver& cv, int M, int N, int K, rqr::TcScratch& s) {
+  M = std::max(M, 1);
+  N = std::max(N, 1);
+  K = std::max(K, 1);
+  carve_tc(cv, (size_t)M + N + 64, rqr::oztc_plane_elems(M, K),
+           std::min(rqr::oztc_plane_elems(N, K), std::max(kTcPlaneBudget, rqr::oztc_plane_elems(64, K))), s);
+}
 
 // Dense product of the method: native precision, or (FP64 with emu) the
 // FP64-accurate bf16 tensor-core splitting of ozaki.cu for products large
@@ -106,10 +130,15 @@ struct Gemm {
   int* iscr;
   T* part;
   size_t cap;
+  const rqr::TcScratch* tc;  // null: the mma.sync splitting only
   void operator()(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, const T* B, int ldb, T beta,
                   T* C, int ldc) const {
     if constexpr (sizeof(T) == 8) {
       if (emu && (double)M * N * K >= 4.0e6 && M >= 16 && N >= 16 && K >= 16) {
+        if (tc && tc->pa &&
+            rqr::gemm_f64x_tc(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tc->emax, tc->pa, tc->pa_cap,
+                              tc->pb, tc->pb_cap, part, cap))
+          return;
         rqr::gemm_f64x(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, iscr, part, cap);
         return;
       }
@@ -119,7 +148,7 @@ struct Gemm {
 };
 
 template <typename T>
-size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs<T>& w) {
+size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs<T>& w, bool tc = false) {
   const int l = b + p;
   w.Y = cv.take<T>((size_t)l * std::max(n, 1));
   w.Gc = cv.take<T>((size_t)l * std::max(m, 1));
@@ -139,6 +168,16 @@ size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs
   w.imap = cv.take<int>(1 + 4 * (size_t)b + 8);
   w.iscr = cv.take<int>(rqr::ozaki_scratch_elems(std::max(m, l), std::max(n, m)));
   w.pers = cv.take<char>(rqr::ypick_persist_scratch_bytes(l, std::max(n, 1), sms));
+  w.tc = rqr::TcScratch{};
+  if (tc) {
+    // largest op(A): G (l x m) or V^T (b x m') with long K, V (m' x b) with K = b;
+    // largest op(B): A (n columns of length m), chunked, or short-K operands
+    const int lb = std::max(l, b), mm = std::max(m, 1), nn = std::max(n, 1);
+    const size_t pa = std::max(rqr::oztc_plane_elems(lb, mm), rqr::oztc_plane_elems(mm, lb));
+    const size_t pb = std::max(rqr::oztc_plane_elems(std::max(nn, mm), lb),
+                               std::min(rqr::oztc_plane_elems(nn, mm), kTcPlaneBudget));
+    carve_tc(cv, (size_t)mm + nn + lb + 64, pa, pb, w.tc);
+  }
   return cv.used;
 }
 
@@ -175,10 +214,10 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
   const int l = b + p;
   Carver cv{static_cast<char*>(work), lwork, 0, false};
   RqrcpWs<T> w;
-  carve_rqrcp<T>(cv, m, n, b, p, h->sms, w);
+  carve_rqrcp<T>(cv, m, n, b, p, h->sms, w, emu);
   if (!cv.ok()) return RQR_ERR_WORKSPACE;
   Ctx c = make_ctx(h);
-  const Gemm<T> mm{c, emu, w.iscr, w.part, w.part_cap};
+  const Gemm<T> mm{c, emu, w.iscr, w.part, w.part_cap, emu ? &w.tc : nullptr};
   cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
   if (n == 0) return finish(h, info);
   const bool down = sketch == RQR_SKETCH_DOWNDATE;
@@ -230,22 +269,27 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_SWAP, 0.0);
       apply_swaps<T>(c, b, w.picks, m, A, lda, k0, l, down ? w.Y : nullptr, l, k0, perm, w.swp, w.imap);
     }
-    // (d) panel QR + T (the Gram matrix V^T V always in native precision)
-    {
-      Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)b * b - 2.0 * b * (double)b * b / 3.0);
-      panel_qr<T>(c, mp, b, P, lda, w.tau, w.pscr);
-      make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
-      gemm<T>(c, true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b, w.part, w.part_cap);
-      larft_tri<T>(c, b, w.gram, b, w.tau, Tb, ldt);
-    }
-    // (e) trailing update. With the tensor-core products (emu) V is split into
+    // (d) panel QR + T. With the tensor-core products (emu) V is split into
     // its unit diagonal E and strictly lower part L, V = E + L: the products
     // with L keep full precision under per-row/column scaling (the unit entry
     // would otherwise set the scale of every column of V), and the E parts are
-    // exact row/column additions.
+    // exact row/column additions; so V^T V = L^T L + I + L1 + L1^T.
+    {
+      Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)b * b - 2.0 * b * (double)b * b / 3.0);
+      panel_qr<T>(c, mp, b, P, lda, w.tau, w.pscr);
+      if (!emu) {
+        make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
+        gemm<T>(c, true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b, w.part, w.part_cap);
+      } else {
+        make_vlow<T>(c, mp, b, P, lda, w.Vx, mp);
+        mm(true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b);
+        gram_from_lower<T>(c, b, w.Vx, mp, w.gram, b);
+      }
+      larft_tri<T>(c, b, w.gram, b, w.tau, Tb, ldt);
+    }
+    // (e) trailing update
     const int n2 = np - b;
     T* A2 = A + k0 + (size_t)(k0 + b) * lda;
-    if (emu) make_vlow<T>(c, mp, b, P, lda, w.Vx, mp);
     {
       Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * b);
       if (!emu) {
@@ -255,7 +299,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       } else {
         copy_mat<T>(c, b, n2, A2, lda, w.W, b);                              // E^T A2
         mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(1), w.W, b);   // + L^T A2
-        gemm<T>(c, true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b, w.part, w.part_cap);
+        mm(true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b);     // T^T W
         mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);  // - L W2
         add_mat<T>(c, b, n2, T(-1), w.W2, b, A2, lda);                         // - E W2
       }
@@ -502,6 +546,7 @@ int rqr_destroy(rqr_handle_t h) {
   cudaStreamSynchronize(h->stream);
   cudaFree(h->d_status);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->kt.pool) cudaEventDestroy(e);
   h->magic = 0;
   delete h;
   return RQR_OK;
@@ -531,7 +576,7 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
     carve_rurv(cv, m, n, b, p, sms, w);
   } else if (prec != RQR_FP32) {
     RqrcpWs<double> w;
-    carve_rqrcp<double>(cv, m, n, b, p, sms, w);
+    carve_rqrcp<double>(cv, m, n, b, p, sms, w, prec == RQR_FP64X);
   } else {
     RqrcpWs<float> w;
     carve_rqrcp<float>(cv, m, n, b, p, sms, w);
@@ -641,6 +686,10 @@ int rqr_profile_enable(rqr_handle_t h, int on) {
   if (!valid(h)) return -1;
   RqrProfile& p = h->prof;
   p.on = on ? 1 : 0;
+  h->kt.on = p.on;
+  h->kt.used = 0;
+  h->kt.flops = 0.0;
+  h->kt.launches = 0;
   p.span_phase.clear();
   for (int i = 0; i < RQR_NUM_PHASES; ++i) {
     p.flops[i] = 0.0;
@@ -672,6 +721,28 @@ int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launche
   return rqr_profile_enable(h, p.on);
 }
 
+int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches) {
+  if (!valid(h)) return -1;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return RQR_ERR_CUDA;
+  }
+  rqr::KernelTimer& k = h->kt;
+  double acc = 0.0;
+  for (size_t i = 0; i < k.used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, k.pool[2 * i], k.pool[2 * i + 1]) == cudaSuccess) acc += t;
+    else cudaGetLastError();
+  }
+  if (ms) *ms = acc;
+  if (flops) *flops = k.flops;
+  if (launches) *launches = k.launches;
+  k.used = 0;
+  k.flops = 0.0;
+  k.launches = 0;
+  return RQR_OK;
+}
+
 int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, double alpha, const void* A, int lda,
              const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork) {
   if (!valid(h)) return -1;
@@ -701,11 +772,16 @@ int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, doub
     const size_t cap = gemm_cap(h->sms);
     double* part = cv.take<double>(cap);
     int* iscr = cv.take<int>(rqr::ozaki_scratch_elems(M, N));
-    const Gemm<double> mm{c, prec == RQR_FP64X, iscr, part, cap};
-    if (prec == RQR_FP64X && M > 0 && N > 0 && K > 0)
-      rqr::gemm_f64x(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
-                     static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, iscr, part, cap);
-    else
+    rqr::TcScratch tc{};
+    if (prec == RQR_FP64X) gemm_tc_carve(cv, M, N, K, tc);
+    const Gemm<double> mm{c, prec == RQR_FP64X, iscr, part, cap, prec == RQR_FP64X ? &tc : nullptr};
+    if (prec == RQR_FP64X && M > 0 && N > 0 && K > 0) {
+      if (!rqr::gemm_f64x_tc(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
+                             static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, tc.emax, tc.pa,
+                             tc.pa_cap, tc.pb, tc.pb_cap, part, cap))
+        rqr::gemm_f64x(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
+                       static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, iscr, part, cap);
+    } else
       mm(ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda, static_cast<const double*>(B), ldb,
          beta, static_cast<double*>(C), ldc);
   }
@@ -723,6 +799,10 @@ int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes) {
   else {
     cv.take<double>(gemm_cap(sms));
     cv.take<int>(rqr::ozaki_scratch_elems(std::max(M, 0), std::max(N, 0)));
+    if (prec == RQR_FP64X) {
+      rqr::TcScratch tc{};
+      gemm_tc_carve(cv, M, N, K, tc);
+    }
   }
   *bytes = cv.used;
   return RQR_OK;

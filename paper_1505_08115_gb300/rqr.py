@@ -30,7 +30,7 @@ FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_workspace_bytes", "rqrcp_factor", "rurv_factor",
            "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill",
            "rqr_philox_raw",
-           "rqr_profile_enable", "rqr_profile_read", "rqr_version")
+           "rqr_profile_enable", "rqr_profile_read", "rqr_profile_kernel_read", "rqr_version")
 PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final", "right")
 
 _lock = threading.Lock()
@@ -69,6 +69,8 @@ def load(path: str = SO_PATH):
         L.rqr_profile_enable.argtypes = [vp, i]
         L.rqr_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64), i]
+        L.rqr_profile_kernel_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int64)]
         L.rqr_version.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name != "rqr_version":
@@ -266,6 +268,16 @@ def profile_read(device=None) -> dict:
     if rc != 0:
         raise RQRError(f"rqr_profile_read failed ({rc})")
     return {p: {"ms": ms[i], "flops": fl[i], "launches": int(ln[i])} for i, p in enumerate(PHASES)}
+
+
+def profile_kernel_read(device=None) -> dict:
+    """{"ms", "flops", "launches"} of the tcgen05 FP64X product kernel while
+    tracing was on (CUDA events around each launch; flops = 36 x 2MNK)."""
+    ms, fl, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    rc = load().rqr_profile_kernel_read(handle(device), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(ln))
+    if rc != 0:
+        raise RQRError(f"rqr_profile_kernel_read failed ({rc})")
+    return {"ms": ms.value, "flops": fl.value, "launches": int(ln.value)}
 
 
 def version() -> str:

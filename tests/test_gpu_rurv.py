@@ -7,8 +7,12 @@ that reduces l samples to b, which differs between the two sides. What both
 sides fix uniquely, and what is compared here, are invariants of each block
 row: the singular values of every diagonal block R(k0:k1, k0:k1), the
 Frobenius norm of every off-diagonal block row R(k0:k1, k1:n), and of every
-trailing block R(k:n, k:n). Tolerance 1e-9 relative to ||A||_2: the subspace
-is determined up to u / gap, and the test inputs keep gaps above 1e-3.
+trailing block R(k:n, k:n). Tolerance 1e-9 relative to ||A||_2, widened at a
+block boundary k1 where the spectrum has only a small absolute gap
+g = sigma_{k1-1} - sigma_{k1}: a block's subspace moves by about u ||A|| / g
+under rounding, and through the sketch and the power step the off-diagonal
+norm by up to 1e3 u ||A||^2 / g (measured on the oracle itself: perturbing A
+by 1e-16 relative moves it by up to 7e-9 on the S-curve case, g = 2.6e-6).
 The factorization bounds A P = Q R with Q, P orthonormal to 1e-13 are checked
 on the GPU's own outputs.
 """
@@ -78,11 +82,16 @@ def test_rurv_parity(m, n, b, p, q, fam):
     assert np.linalg.norm(A @ P - Q[:, :n] @ R) <= 1e-13 * nA
     assert np.linalg.norm(Q.T @ Q - np.eye(m)) <= 1e-13
     assert np.linalg.norm(P.T @ P - np.eye(n)) <= 1e-13
-    nA2 = np.linalg.norm(A, 2)
+    sv = np.linalg.svd(A, compute_uv=False)
+    nA2 = sv[0]
     R0 = np.triu(F0)[:n]
-    for (s, off, tail), (s0, off0, tail0) in zip(block_invariants(R, b), block_invariants(R0, b)):
+    starts = inputs.block_starts(n, b)
+    for k0, (s, off, tail), (s0, off0, tail0) in zip(starts, block_invariants(R, b), block_invariants(R0, b)):
+        k1 = min(n, k0 + b)
+        gap = sv[k1 - 1] - sv[k1] if k1 < n else nA2
+        tol = max(1e-9 * nA2, 1e3 * 2.0 ** -53 * nA2 ** 2 / max(gap, 1e-300))
         assert np.abs(s - s0).max() <= 1e-9 * nA2
-        assert abs(off - off0) <= 1e-9 * nA2
+        assert abs(off - off0) <= tol
         assert abs(tail - tail0) <= 1e-9 * nA2
     # the GPU's S blocks are stored like the oracle's: strictly lower part only
     assert np.all(np.triu(WV) == 0)
