@@ -51,6 +51,7 @@ constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 16, TC_ND = 8, TC_NS = 4, TC_WIN 
 // one TMA producer warp, one MMA warp.
 constexpr int TC_EPI_WARPS = 16, TC_PROD_WARP = 16, TC_MMA_WARP = 17, TC_THREADS = 576;
 constexpr int TC_EPI_COLS = TC_BN / (TC_EPI_WARPS / 4);  // 16 columns per epilogue warp
+constexpr int TC_CCH = 4;                                 // C values loaded together in the epilogue
 constexpr uint32_t TC_A_BYTES = TC_ND * TC_BM * TC_BK * 2;    // 32 KB
 constexpr uint32_t TC_B_BYTES = TC_ND * TC_BN * TC_BK * 2;    // 16 KB
 constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KB
@@ -228,6 +229,61 @@ __global__ void k_split_contig(int R, int K, const double* __restrict__ X, int l
     const double x0 = x[k];
     const double x1 = k + 1 < K ? x[k + 1] : 0.0;
     store_digit_pair(planes, pstride, ((size_t)r * kld + k) / 2, x0, x1, e);
+  }
+}
+
+// Digit planes of long contiguous rows (element (r, k) at X[k + r ld]) with
+// the row exponent computed in the same launch: one CTA per row, a first pass
+// for the largest exponent (block max), a second pass (served mostly from L2)
+// that writes the digits; four 16-byte loads in flight per thread.
+constexpr int SPLIT_T = 256;
+__global__ void __launch_bounds__(SPLIT_T) k_split_rows(int R, int K, const double* __restrict__ X, int ld,
+                                                        int* emax_out, uint32_t* planes, int kld) {
+  __shared__ int wmax[SPLIT_T / 32];
+  const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* x = X + (size_t)r * ld;
+  // pass 1: largest biased exponent of the row
+  int e = 0;
+  const bool al16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  if (al16) {
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    const int K2 = K / 2;
+    for (int k = tid; k < K2; k += 4 * SPLIT_T) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = (k + u * SPLIT_T < K2) ? x2[k + u * SPLIT_T] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e = max(e, max(biased_exp_tc(v[u].x), biased_exp_tc(v[u].y)));
+    }
+    if ((K & 1) && tid == 0) e = max(e, biased_exp_tc(x[K - 1]));
+  } else {
+    for (int k = tid; k < K; k += SPLIT_T) e = max(e, biased_exp_tc(x[k]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) wmax[warp] = e;
+  __syncthreads();
+  int emx = 0;
+#pragma unroll
+  for (int w = 0; w < SPLIT_T / 32; ++w) emx = max(emx, wmax[w]);
+  if (tid == 0) emax_out[r] = emx;
+  const int sc = scale_exp_tc(emx);
+  // pass 2: digits, two values per thread and step (one 32-bit word per plane)
+  const size_t pstride = (size_t)R * kld / 2;
+  const size_t rbase = (size_t)r * kld / 2;
+  for (int kp = tid; 2 * kp < K; kp += 2 * SPLIT_T) {
+    double a0[2], a1[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int k = 2 * (kp + u * SPLIT_T);
+      a0[u] = k < K ? x[k] : 0.0;
+      a1[u] = k + 1 < K ? x[k + 1] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int k = 2 * (kp + u * SPLIT_T);
+      if (k < K) store_digit_pair(planes, pstride, rbase + k / 2, a0[u], a1[u], sc);
+    }
   }
 }
 
@@ -513,21 +569,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int i = m0 + row;
       if (i < a.M) {
         const int ei = scale_exp_tc(a.emaxA[i]);
+        const bool needc = mode == 3 || mode == 4 || mode == 6;
+        // chunks of TC_CCH columns: the C loads of a chunk are issued together
+        // (one memory latency per chunk instead of one per element)
 #pragma unroll
-        for (int c = 0; c < TC_EPI_COLS; ++c) {
-          const int j = n0 + cg * TC_EPI_COLS + c;
-          if (j >= a.N) continue;
-          const double v = z_to_double(H[c], m6_fixed(M6[c]), ei + scale_exp_tc(a.emaxB[j]));
-          const double nv = __longlong_as_double(__double_as_longlong(v) ^ (1ll << 63));  // -v, exact
-          double* cp = a.C + i + (size_t)j * a.ldc;
-          switch (mode) {
-            case 0: a.part[(size_t)(t % a.S) * a.M * a.N + i + (size_t)j * a.M] = v; break;
-            case 1: *cp = v; break;
-            case 2: *cp = nv; break;
-            case 3: *cp = *cp + v; break;
-            case 4: *cp = *cp + nv; break;
-            case 5: *cp = a.alpha * v; break;
-            default: *cp = fma(a.alpha, v, a.beta * *cp); break;
+        for (int h = 0; h < TC_EPI_COLS; h += TC_CCH) {
+          double cold[TC_CCH];
+#pragma unroll
+          for (int c = 0; c < TC_CCH; ++c) {
+            const int j = n0 + cg * TC_EPI_COLS + h + c;
+            cold[c] = (needc && j < a.N) ? a.C[i + (size_t)j * a.ldc] : 0.0;
+          }
+#pragma unroll
+          for (int c = 0; c < TC_CCH; ++c) {
+            const int j = n0 + cg * TC_EPI_COLS + h + c;
+            if (j >= a.N) continue;
+            const double v = z_to_double(H[h + c], m6_fixed(M6[h + c]), ei + scale_exp_tc(a.emaxB[j]));
+            const double nv = __longlong_as_double(__double_as_longlong(v) ^ (1ll << 63));  // -v, exact
+            double* cp = a.C + i + (size_t)j * a.ldc;
+            switch (mode) {
+              case 0: a.part[(size_t)(t % a.S) * a.M * a.N + i + (size_t)j * a.M] = v; break;
+              case 1: *cp = v; break;
+              case 2: *cp = nv; break;
+              case 3: *cp = cold[c] + v; break;
+              case 4: *cp = cold[c] + nv; break;
+              case 5: *cp = a.alpha * v; break;
+              default: *cp = fma(a.alpha, v, a.beta * cold[c]); break;
+            }
           }
         }
       }
@@ -592,6 +660,12 @@ inline int kld_of(int K) { return (K + 7) & ~7; }
 // X[k + r ld]; else at X[r + k ld]).
 void split_operand(const Ctx& c, bool contig, int R, int K, const double* X, int ld, int* emax, uint16_t* planes) {
   const int kld = kld_of(K);
+  if (contig && K >= 2048) {
+    // long rows: exponent and digits in one launch, one CTA per row
+    k_split_rows<<<R, SPLIT_T, 0, c.stream>>>(R, K, X, ld, emax, reinterpret_cast<uint32_t*>(planes), kld);
+    note_launch(c);
+    return;
+  }
   cudaMemsetAsync(emax, 0, sizeof(int) * R, c.stream);
   const int kch = 4096;
   dim3 ge(contig ? ceil_div(R, 8) : ceil_div(R, 128), ceil_div(K, kch));

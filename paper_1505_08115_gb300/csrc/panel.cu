@@ -294,50 +294,65 @@ __global__ void __launch_bounds__(PT) k_qrcp_apply(int j, int nsteps, PanelArgs 
 
 // ------------------------------------------------------------ T factor
 // T(0:j, j) = -tau_j T(0:j, 0:j) (V^T V)(0:j, j), T(j, j) = tau_j (Sec. 5.1),
-// one CTA. T lives in shared memory when it fits (kb <= 160 in FP64), the
-// Gram column of the current step is staged in shared memory, and two threads
-// share each row's dot product (two independent accumulation chains).
+// one CTA. When kb^2 values fit in shared memory (kb <= 160 in FP64) the
+// strict upper triangle of the Gram matrix and the upper triangle of T are
+// kept there packed by columns (column l of T at l(l+1)/2, column j of the
+// Gram matrix at j(j-1)/2), so a step reads no global memory; two threads
+// share each row's dot product. Otherwise T is built in global memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__ gram, int ldg, const T* tau, T* Tm,
                                                    int ldt, int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* gcol = reinterpret_cast<T*>(smem_raw);  // [kb]
-  T* St = gcol + kb;
   const int tid = threadIdx.x;
-  T* W = use_smem ? St : Tm;
-  const int ldw = use_smem ? kb : ldt;
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e % kb, c = e / kb;
-    W[i + (size_t)c * ldw] = T(0);
-  }
-  for (int j = 0; j < kb; ++j) {
-    for (int r = tid; r < j; r += blockDim.x) gcol[r] = gram[r + (size_t)j * ldg];
+  if (use_smem) {
+    T* Tp = reinterpret_cast<T*>(smem_raw);     // kb (kb + 1) / 2
+    T* Gp = Tp + (size_t)kb * (kb + 1) / 2;     // kb (kb - 1) / 2
+    for (int j = 1; j < kb; ++j)
+      for (int l = tid; l < j; l += blockDim.x) Gp[(size_t)j * (j - 1) / 2 + l] = gram[l + (size_t)j * ldg];
     __syncthreads();
-    const T tj = tau[j];
-    // rows i = pair index, two threads per row (adjacent lanes) split l
-    for (int base = 0; base < j; base += (int)blockDim.x / 2) {
-      const int i = base + (tid >> 1), h = tid & 1;
-      T s0 = T(0), s1 = T(0);
-      if (i < j) {
-        int l = i + h;
-        for (; l + 2 < j; l += 4) {
-          s0 += W[i + (size_t)l * ldw] * gcol[l];
-          s1 += W[i + (size_t)(l + 2) * ldw] * gcol[l + 2];
+    for (int j = 0; j < kb; ++j) {
+      const T tj = tau[j];
+      const T* gj = Gp + (size_t)j * (j - 1) / 2;
+      T* tjcol = Tp + (size_t)j * (j + 1) / 2;
+      for (int base = 0; base < j; base += (int)blockDim.x / 2) {
+        const int i = base + (tid >> 1), h = tid & 1;
+        T s0 = T(0), s1 = T(0);
+        if (i < j) {
+          int l = i + h;
+          for (; l + 2 < j; l += 4) {
+            s0 += Tp[(size_t)l * (l + 1) / 2 + i] * gj[l];
+            s1 += Tp[(size_t)(l + 2) * (l + 3) / 2 + i] * gj[l + 2];
+          }
+          if (l < j) s0 += Tp[(size_t)l * (l + 1) / 2 + i] * gj[l];
         }
-        if (l < j) s0 += W[i + (size_t)l * ldw] * gcol[l];
+        T s = s0 + s1;
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (i < j && h == 0) tjcol[i] = -tj * s;
       }
-      T s = s0 + s1;
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      if (i < j && h == 0) W[i + (size_t)j * ldw] = -tj * s;
+      if (tid == 0) tjcol[j] = tj;
+      __syncthreads();
     }
-    if (tid == 0) W[j + (size_t)j * ldw] = tj;
-    __syncthreads();
-  }
-  if (use_smem)
     for (int e = tid; e < kb * kb; e += blockDim.x) {
       const int i = e % kb, c = e / kb;
-      Tm[i + (size_t)c * ldt] = St[i + (size_t)c * kb];
+      Tm[i + (size_t)c * ldt] = i <= c ? Tp[(size_t)c * (c + 1) / 2 + i] : T(0);
     }
+    return;
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e % kb, c = e / kb;
+    Tm[i + (size_t)c * ldt] = T(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const T tj = tau[j];
+    for (int i = tid; i < j; i += blockDim.x) {
+      T s = T(0);
+      for (int l = i; l < j; ++l) s += Tm[i + (size_t)l * ldt] * gram[l + (size_t)j * ldg];
+      Tm[i + (size_t)j * ldt] = -tj * s;
+    }
+    if (tid == 0) Tm[j + (size_t)j * ldt] = tj;
+    __syncthreads();
+  }
 }
 
 // Gram matrix of V = E + L from the Gram matrix of its strictly lower part:
@@ -496,9 +511,9 @@ void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int3
 template <typename T>
 void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt) {
   if (kb <= 0) return;
-  const size_t need = sizeof(T) * ((size_t)kb * kb + kb);
+  const size_t need = sizeof(T) * (size_t)kb * kb;
   const int use_smem = need <= 200 * 1024 ? 1 : 0;
-  const size_t sm = use_smem ? need : sizeof(T) * (size_t)kb;
+  const size_t sm = use_smem ? need : 0;
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_larft_tri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_larft_tri<T><<<1, 256, sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt, use_smem);
   note_launch(c);

@@ -221,60 +221,53 @@ __global__ void __launch_bounds__(YT) k_ypick_step(int j, YArgs a, const T* __re
 }
 
 // ------------------------------------------------------------ swaps
-// One warp replays the swaps (j, picks[j]) on a list of touched positions and
+// Replays the swaps (j, picks[j]), j = 0..kb-1, on the touched positions and
 // emits (dst, src) pairs of the net permutation: imap[0] = count, then pairs.
+// Positions below kb map to their own slot; the at most kb others go through
+// an open-addressing hash table in shared memory, so the replay is O(kb).
+constexpr int kMapHash = 2048;  // >= 4 kb for kb <= 512
 __global__ void k_build_map(int kb, const int* picks, int* imap) {
   extern __shared__ int sh[];
-  int* pos = sh;            // [2kb]
-  int* cont = sh + 2 * kb;  // [2kb]
-  __shared__ int cnt;
-  const int lane = threadIdx.x;
-  if (lane == 0) cnt = 0;
-  __syncwarp();
-  auto find = [&](int p) -> int {
-    int found = -1;
-    for (int base = 0; base < cnt; base += 32) {
-      const int e = base + lane;
-      const unsigned m = __ballot_sync(0xffffffffu, e < cnt && pos[e] == p);
-      if (m) {
-        found = base + __ffs(m) - 1;
-        break;
-      }
+  int* cont = sh;               // [kb] content of positions 0..kb-1
+  int* hkey = sh + kb;          // [kMapHash] position, -1 = empty
+  int* hval = hkey + kMapHash;  // [kMapHash] content
+  for (int e = threadIdx.x; e < kb; e += blockDim.x) cont[e] = e;
+  for (int e = threadIdx.x; e < kMapHash; e += blockDim.x) hkey[e] = -1;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  auto slot = [&](int p) -> int* {
+    if (p < kb) return cont + p;
+    unsigned h = ((unsigned)p * 2654435761u) & (kMapHash - 1);
+    while (hkey[h] != -1 && hkey[h] != p) h = (h + 1) & (kMapHash - 1);
+    if (hkey[h] == -1) {
+      hkey[h] = p;
+      hval[h] = p;
     }
-    if (found < 0) {
-      if (lane == 0) {
-        pos[cnt] = p;
-        cont[cnt] = p;
-        cnt = cnt + 1;
-      }
-      __syncwarp();
-      found = cnt - 1;
-    }
-    __syncwarp();
-    return found;
+    return hval + h;
   };
   for (int j = 0; j < kb; ++j) {
     const int pk = picks[j];
     if (pk == j) continue;
-    const int ea = find(j);
-    const int eb = find(pk);
-    if (lane == 0) {
-      const int t = cont[ea];
-      cont[ea] = cont[eb];
-      cont[eb] = t;
+    int* a = slot(j);
+    int* b = slot(pk);
+    const int t = *a;
+    *a = *b;
+    *b = t;
+  }
+  int n = 0;
+  for (int e = 0; e < kb; ++e)
+    if (cont[e] != e) {
+      imap[1 + 2 * n] = e;
+      imap[2 + 2 * n] = cont[e];
+      ++n;
     }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    int n = 0;
-    for (int e = 0; e < cnt; ++e)
-      if (pos[e] != cont[e]) {
-        imap[1 + 2 * n] = pos[e];
-        imap[2 + 2 * n] = cont[e];
-        ++n;
-      }
-    imap[0] = n;
-  }
+  for (int h = 0; h < kMapHash; ++h)
+    if (hkey[h] != -1 && hval[h] != hkey[h]) {
+      imap[1 + 2 * n] = hkey[h];
+      imap[2 + 2 * n] = hval[h];
+      ++n;
+    }
+  imap[0] = n;
 }
 
 template <typename T>
@@ -357,7 +350,7 @@ template <typename T>
 void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy, int y0,
                  int32_t* perm, T* tmp, int* imap) {
   if (kb <= 0) return;
-  k_build_map<<<1, 32, sizeof(int) * 4 * kb, c.stream>>>(kb, picks, imap);
+  k_build_map<<<1, 256, sizeof(int) * ((size_t)kb + 2 * kMapHash), c.stream>>>(kb, picks, imap);
   T* tmpA = tmp;
   T* tmpY = tmpA + (size_t)m * 2 * kb;
   int32_t* tmpP = reinterpret_cast<int32_t*>(tmpY + (size_t)l * 2 * kb);
