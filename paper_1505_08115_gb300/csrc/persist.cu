@@ -23,6 +23,7 @@ namespace rqr {
 namespace {
 
 constexpr int PT = 256, PNW = PT / 32;
+constexpr double kRecompute = 1.0 / 1024.0;  // pivot norms: recompute below this fraction of the last exact one
 
 struct GridSync {
   unsigned count;  // arrivals so far (zeroed before the launch)
@@ -81,7 +82,7 @@ struct PArgs {
   T* cand_n;    // [2][C] candidate squared norms (step parity)
   int* cand_p;  // [2][C] candidate positions
   T* candcol;   // [2][C][l] candidate columns
-  T* colbuf;    // [2][l] column leaving the pivot position
+  T* colbuf;    // [2][l + 2] column leaving the pivot position, its norm and reference norm
   GridSync* gs;
   int* status;
 };
@@ -98,12 +99,20 @@ __device__ __forceinline__ bool better(T n, int p, T bn, int bp) {
 // the C published candidates (same data and order in every CTA, so the same
 // winner), builds the reflector from the winner's values and applies it to its
 // own columns. One barrier per step and no serial phase in a single CTA.
+// The squared norms of rows s+1.. are downdated from those of rows s..
+// (the reflector keeps the norm of rows s..: |y(s+1:)|^2 = |y(s:)|^2 - y_s^2,
+// y_s after the update) and recomputed exactly from the column whenever the
+// downdated value has fallen below kRecompute of the last exact one, which
+// bounds the downdate's relative error by about u / kRecompute per step.
 template <typename T>
 __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = a.l, C = gridDim.x;
   T* tile = reinterpret_cast<T*>(smem_raw);  // [per][l]
   T* v = tile + (size_t)a.per * l;            // [l]
+  T* nrm = v + l;                             // [per] squared norm of rows s.. of each column
+  T* ref = nrm + a.per;                       // [per] the last exactly computed squared norm
+  const int LB = l + 2;                       // colbuf stride: values, norm, reference
   __shared__ T shn[PNW];
   __shared__ int shp[PNW], shq[PNW];
   __shared__ T s_tau;
@@ -123,6 +132,10 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     T ss = T(0);
     for (int r = lane; r < l; r += 32) ss += y[r] * y[r];
     ss = warp_sum(ss);
+    if (lane == 0) {
+      nrm[pl] = ss;
+      ref[pl] = ss;
+    }
     if (better(ss, lo + pl, wn, wp)) {
       wn = ss;
       wp = lo + pl;
@@ -149,8 +162,13 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     }
     if (bp >= lo && bp < hi)
       for (int r = s + tid; r < l; r += PT) a.candcol[((size_t)par * C + q) * l + r] = tile[(size_t)(bp - lo) * l + r];
-    if (s >= lo && s < hi)
-      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * l + r] = tile[(size_t)(s - lo) * l + r];
+    if (s >= lo && s < hi) {
+      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * LB + r] = tile[(size_t)(s - lo) * l + r];
+      if (tid == 0) {
+        a.colbuf[(size_t)par * LB + l] = nrm[s - lo];
+        a.colbuf[(size_t)par * LB + l + 1] = ref[s - lo];
+      }
+    }
     if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status)) return;
     // ---- global winner (every CTA, identical order)
     T cn = T(-1);
@@ -222,7 +240,12 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       }
     } else if (pw != s && pw >= lo && pw < hi) {
       // the column that was at position s moves to the winner's position
-      for (int r = s + tid - 32; r < l; r += PT - 32) tile[(size_t)(pw - lo) * l + r] = __ldcg(a.colbuf + (size_t)par * l + r);
+      for (int r = s + tid - 32; r < l; r += PT - 32)
+        tile[(size_t)(pw - lo) * l + r] = __ldcg(a.colbuf + (size_t)par * LB + r);
+      if (tid == 32) {
+        nrm[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l);
+        ref[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l + 1);
+      }
     }
     __syncthreads();
     if (s + 1 >= a.bsteps) break;
@@ -235,15 +258,27 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       T dot = T(0);
       for (int r = lane; r < L; r += 32) dot += v[r] * y[r];
       dot = warp_sum(dot) * tau;
-      T ss = T(0);
+      T y0 = T(0);
       for (int r = lane; r < L; r += 32) {
         const T nx = y[r] - dot * v[r];
         y[r] = nx;
-        if (r >= 1) ss += nx * nx;
+        if (r == 0) y0 = nx;
       }
-      ss = warp_sum(ss);
-      if (better(ss, lo + pl, wn, wp)) {
-        wn = ss;
+      y0 = __shfl_sync(0xffffffffu, y0, 0);
+      const T rf = ref[pl];
+      T nn = nrm[pl] - y0 * y0;
+      if (!(nn > kRecompute * rf)) {
+        // exact squared norm of rows s+1.. (the downdate lost too many digits)
+        __syncwarp();
+        T ss = T(0);
+        for (int r = 1 + lane; r < L; r += 32) ss += y[r] * y[r];
+        nn = warp_sum(ss);
+        if (lane == 0) ref[pl] = nn;
+      }
+      __syncwarp();
+      if (lane == 0) nrm[pl] = nn;
+      if (better(nn, lo + pl, wn, wp)) {
+        wn = nn;
         wp = lo + pl;
       }
     }
@@ -449,7 +484,7 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
   C = std::max(1, std::min(sms, ceil_div(np, 8)));
   per = ceil_div(std::max(np, 1), C);
   C = ceil_div(std::max(np, 1), per);
-  return sizeof(double) * ((size_t)per * l + l);
+  return sizeof(double) * ((size_t)per * l + l + 2 * (size_t)per);
 }
 
 size_t ypick_persist_scratch_bytes(int l, int np, int sms) {
@@ -484,7 +519,7 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
   T* cand_n = reinterpret_cast<T*>(p);
   T* candcol = cand_n + 2 * (size_t)C;
   T* colbuf = candcol + 2 * (size_t)C * l;
-  int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)l + 8);
+  int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)(l + 2) + 8);
   cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
   PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_n, cand_p, candcol, colbuf, gs, c.status};
   void* args[] = {&a};
