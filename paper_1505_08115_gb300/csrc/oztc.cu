@@ -9,19 +9,22 @@
 //    Plane p stores d_p 2^(-7p) in bf16 (exact: at most 7 significant bits),
 //    K-contiguous: planes[p][r][k], row stride kld.
 // 2. Products (k_oztc). A 128 x 64 output tile, K consumed 16 at a time.
-//    For each k16 step all 36 digit pairs p + q <= 7 are multiplied
-//    (tcgen05.mma.kind::f16, M = 128, N = 64, K = 16) into seven TMEM slots:
-//    slot a = p + q for a <= 5, slot 6 for p + q in 6..7. Pairs of slot a
-//    carry the common factor 2^(-7a); with |d| <= 127 and at most a + 1 pairs
-//    per slot, a slot's sum over a window of 128 K is below
-//    (a + 1) 128 127^2 2^(-7a) < 2^(24 - 7a), so slots 0..5 hold exact
-//    integers S_a 2^(-7a) in FP32. Slot 6 (weights 2^-42 and below relative to
-//    the leading term) is accumulated in FP32; its rounding stays below
-//    2^-58 of the product's scale.
-// 3. Drain (epilogue warps), once per window of 128 K: the exact slots are
+//    For each k16 step all 36 digit pairs p + q <= 7 are multiplied into
+//    eight TMEM slots of 64 columns, slot a = p + q. Since the B planes sit
+//    next to each other in shared memory and the slots next to each other in
+//    TMEM, the pairs (p, q0..q0+3) are ONE tcgen05.mma.kind::f16 with M = 128,
+//    N = 256 (A plane p against B planes q0..q0+3 into slots p+q0..p+q0+3):
+//    12 MMAs per k16 step, and each A plane is read from shared memory 1 or 2
+//    times instead of 8 - p. Pairs of slot a carry the common factor 2^(-7a);
+//    with |d| <= 127 and at most a + 1 pairs per slot, a slot's sum over a
+//    window of 128 K is below (a + 1) 128 127^2 2^(-7a) < 2^(24 - 7a), so every
+//    slot holds an exact integer S_a 2^(-7a) in FP32.
+// 3. Drain (epilogue warps), once per window of 128 K: slots 0..5 are
 //    converted to integers and added into H = sum_{a<=5} S_a 2^(7(5-a))
-//    (int64; below 2^57 per window, at most 64 windows per tile), slot 6 into
-//    a float M6. At the end of the tile the value
+//    (int64; below 2^57 per window, at most 64 windows per tile), slots 6 and 7
+//    (weights 2^-42 and below relative to the leading term) into a float M6,
+//    whose rounding stays below 2^-58 of the product's scale. At the end of
+//    the tile the value
 //      (AB)_ij = 2^(e_i + f_j - 63) (H 2^14 + M6 2^49)
 //    is rounded once to FP64 with integer operations (GB300 runs FP64 at
 //    about two operations per clock per SM, so the epilogue avoids FP64
@@ -150,9 +153,10 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: D FP32, A and B bf16, both K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+// Instruction descriptor: D FP32, A and B bf16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
 
 // ------------------------------------------------------------------ digits
 // Scale exponent e with |x| < 2^e for every x of a row whose largest
@@ -490,17 +494,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t sa = sbase + s * TC_STAGE_BYTES, sb = sa + TC_A_BYTES;
-            uint32_t fresh = k == w0 ? 0x7Fu : 0u;  // slots not yet written in this window
+            // the first k-step of a window overwrites every slot with plane
+            // p = 0 (it reaches slots 0..7); everything else accumulates
 #pragma unroll
             for (int p = 0; p < TC_ND; ++p) {
               const uint64_t ad = sdesc_sw32(sa + p * (TC_BM * TC_BK * 2));
+              const uint32_t acc = (k == w0 && p == 0) ? 0u : 1u;
 #pragma unroll
-              for (int q = 0; q < TC_ND - p; ++q) {
-                const int slot = p + q < 6 ? p + q : 6;
-                const uint64_t bd = sdesc_sw32(sb + q * (TC_BN * TC_BK * 2));
-                const uint32_t acc = (fresh >> slot) & 1u ? 0u : 1u;
-                fresh &= ~(1u << slot);
-                tc_mma(tmem + slot * TC_BN, ad, bd, kIdesc, acc);
+              for (int q0 = 0; q0 < TC_ND - p; q0 += 4) {
+                const int nq = TC_ND - p - q0 < 4 ? TC_ND - p - q0 : 4;
+                const uint64_t bd = sdesc_sw32(sb + q0 * (TC_BN * TC_BK * 2));
+                tc_mma(tmem + (p + q0) * TC_BN, ad, bd, idesc_n(TC_BN * nq), acc);
               }
             }
             tc_commit(empty(s));
@@ -557,10 +561,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             H[c] += (long long)S << (7 * (5 - s));
           }
         }
-        tc_ld16(tbase + 6 * TC_BN, v);
-        tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < TC_EPI_COLS; ++c) M6[c] += __uint_as_float(v[c]);
+        for (int s = 6; s < 8; ++s) {
+          tc_ld16(tbase + s * TC_BN, v);
+          tc_wait_ld();
+#pragma unroll
+          for (int c = 0; c < TC_EPI_COLS; ++c) M6[c] += __uint_as_float(v[c]);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty);
