@@ -327,6 +327,7 @@ def main():
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"{src} bf16 dense {peak} TF/s (sustained: the kernel runs inside a seconds-long step)",
                 "launches_per_step": kern["launches"] // a.steps, "ms_per_step": kern["ms"] / a.steps,
+                "algorithmic_bytes_per_launch": kern["bytes"] / max(kern["launches"], 1),
                 "fp64_equivalent_tflops": achieved / 36.0, "update_phase_fp64_equivalent_tflops": fp64_eq,
                 "traffic": None}
     else:

@@ -186,9 +186,10 @@ int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launche
 
 /* Waits for the handle's stream, then writes the summed CUDA-event time (ms),
  * the algorithmic tensor-core flops (36 bf16 digit-pair products of 2 M N K
- * each) and the launch count of the tcgen05 FP64X product kernel launched
- * while tracing was on (host outputs, any may be NULL); clears them. */
-int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches);
+ * each), the algorithmic DRAM bytes (both operands' digit planes once, C read
+ * and written) and the launch count of the tcgen05 FP64X product kernel
+ * launched while tracing was on (host outputs, any may be NULL); clears them. */
+int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* Library version string (static storage). */
 const char* rqr_version(void);

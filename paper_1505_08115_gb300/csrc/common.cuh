@@ -21,6 +21,7 @@ struct KernelTimer {
   std::vector<cudaEvent_t> pool;  // 2 events per recorded launch
   size_t used = 0;                // pairs recorded
   double flops = 0.0;             // algorithmic tensor-core flops of the recorded launches
+  double bytes = 0.0;             // algorithmic DRAM bytes of the recorded launches
   int64_t launches = 0;
   // Records the start event of a launch; false when timing is off or an event cannot be made.
   bool start(cudaStream_t s) {
@@ -36,10 +37,11 @@ struct KernelTimer {
     cudaEventRecord(pool[2 * used], s);
     return true;
   }
-  void stop(cudaStream_t s, double fl) {
+  void stop(cudaStream_t s, double fl, double by) {
     cudaEventRecord(pool[2 * used + 1], s);
     ++used;
     flops += fl;
+    bytes += by;
     ++launches;
   }
 };

@@ -770,7 +770,13 @@ bool gemm_f64x_tc(const Ctx& c, bool ta, bool tb, int M, int N, int K, double al
     const int grid = std::min(tiles, c.sms);
     const bool timed = c.kt && c.kt->start(c.stream);
     k_oztc<<<grid, TC_THREADS, TC_SMEM, c.stream>>>(mapA, nn == nc ? mapB : mapBlast, a);
-    if (timed) c.kt->stop(c.stream, 36.0 * 2.0 * (double)M * nn * K);  // 36 digit-pair products
+    if (timed) {
+      // 36 digit-pair products; bytes: both operands' digit planes once (16 B per
+      // element) and C read (beta != 0) and written, or the split-K partials written
+      const double planes = 16.0 * ((double)M + nn) * K;
+      const double cbytes = a.S > 1 ? 8.0 * a.S * M * nn : 8.0 * M * nn * (beta != 0.0 ? 2.0 : 1.0);
+      c.kt->stop(c.stream, 36.0 * 2.0 * (double)M * nn * K, planes + cbytes);
+    }
     note_launch(c);
     if (a.S > 1) {
       const size_t MN = (size_t)M * nn;

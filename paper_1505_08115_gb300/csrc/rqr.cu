@@ -689,6 +689,7 @@ int rqr_profile_enable(rqr_handle_t h, int on) {
   h->kt.on = p.on;
   h->kt.used = 0;
   h->kt.flops = 0.0;
+  h->kt.bytes = 0.0;
   h->kt.launches = 0;
   p.span_phase.clear();
   for (int i = 0; i < RQR_NUM_PHASES; ++i) {
@@ -721,7 +722,7 @@ int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launche
   return rqr_profile_enable(h, p.on);
 }
 
-int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches) {
+int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, double* bytes, int64_t* launches) {
   if (!valid(h)) return -1;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
     cudaGetLastError();
@@ -736,9 +737,11 @@ int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, int64_t* 
   }
   if (ms) *ms = acc;
   if (flops) *flops = k.flops;
+  if (bytes) *bytes = k.bytes;
   if (launches) *launches = k.launches;
   k.used = 0;
   k.flops = 0.0;
+  k.bytes = 0.0;
   k.launches = 0;
   return RQR_OK;
 }

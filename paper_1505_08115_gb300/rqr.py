@@ -70,7 +70,7 @@ def load(path: str = SO_PATH):
         L.rqr_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64), i]
         L.rqr_profile_kernel_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                              ctypes.POINTER(ctypes.c_int64)]
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         L.rqr_version.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name != "rqr_version":
@@ -271,13 +271,15 @@ def profile_read(device=None) -> dict:
 
 
 def profile_kernel_read(device=None) -> dict:
-    """{"ms", "flops", "launches"} of the tcgen05 FP64X product kernel while
-    tracing was on (CUDA events around each launch; flops = 36 x 2MNK)."""
-    ms, fl, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-    rc = load().rqr_profile_kernel_read(handle(device), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(ln))
+    """{"ms", "flops", "bytes", "launches"} of the tcgen05 FP64X product kernel
+    while tracing was on (CUDA events around each launch; flops = 36 x 2MNK;
+    bytes = digit planes read once plus C read and written)."""
+    ms, fl, by, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    rc = load().rqr_profile_kernel_read(handle(device), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by),
+                                        ctypes.byref(ln))
     if rc != 0:
         raise RQRError(f"rqr_profile_kernel_read failed ({rc})")
-    return {"ms": ms.value, "flops": fl.value, "launches": int(ln.value)}
+    return {"ms": ms.value, "flops": fl.value, "bytes": by.value, "launches": int(ln.value)}
 
 
 def version() -> str:
