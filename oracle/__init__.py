@@ -62,6 +62,9 @@ def lib():
             L.orc_rurv.argtypes = [c_int, c_int, d, c_int, c_int, c_int, c_int, c_int, d,
                                    d, c_int, d, c_int, d, c_int]
             L.orc_rurv.restype = c_int
+            L.orc_rurv_diag.argtypes = [c_int, c_int, d, c_int, c_int, c_int, c_int, c_int, d,
+                                        d, c_int, d, c_int, d, c_int, d, c_int, d, c_int]
+            L.orc_rurv_diag.restype = c_int
             L.orc_jacobi_svd.argtypes = [c_int, c_int, d, c_int, d, d, c_int]
             L.orc_jacobi_svd.restype = c_int
             u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -184,6 +187,22 @@ def rurv(A, b, p, q, G, k=0):
     WV = np.zeros((n, n), order="F")
     done = lib().orc_rurv(m, n, _dp(F), m, b, p, q, k, _dp(Gf), _dp(TU), b, _dp(WV), n, _dp(TV), b)
     return F, TU, WV, TV, done
+
+
+def rurv_diag(A, b, p, q, G, k=0):
+    """rurv with diagonalised diagonal blocks (Sec. 6.2, Fig. blockRRQR).
+    Returns (F, TU, WV, TV, DU, DV, ncols); DU, DV (b x n) hold U' and Vt per block."""
+    F = _f64(A)
+    m, n = F.shape
+    Gf = np.ascontiguousarray(G, dtype=np.float64).ravel()
+    TU = np.zeros((b, n), order="F")
+    TV = np.zeros((b, n), order="F")
+    WV = np.zeros((n, n), order="F")
+    DU = np.zeros((b, n), order="F")
+    DV = np.zeros((b, n), order="F")
+    done = lib().orc_rurv_diag(m, n, _dp(F), m, b, p, q, k, _dp(Gf), _dp(TU), b, _dp(WV), n, _dp(TV), b,
+                               _dp(DU), b, _dp(DV), b)
+    return F, TU, WV, TV, DU, DV, done
 
 
 def jacobi_svd(M):

@@ -447,8 +447,85 @@ static int thin_qr(int r, int c, const double* Z, int ldz, double* Q, int ldq, d
 }
 
 /* ------------------------------------------------ Sec. 4.2, 6.3, 6.4 */
+/* Sec. 6.2 (Fig. blockRRQR): diagonalise the bi x bi diagonal block R11 of the
+ * block that starts at k0, after its left QR and trailing update. The SVD is
+ * R11 = U' D Vt^T: one-sided Jacobi on M = R11^T gives M J = Vt D with J = U'
+ * (columns sorted by descending norm); the columns of Vt are those of M J over
+ * their norms, and a zero column is replaced by the first unit vector that
+ * Gram-Schmidt (twice) against the columns already set leaves with norm above
+ * 1/2. Then A(0:k0, block) <- A(0:k0, block) Vt, R12 <- U'^T R12, R11 <- D
+ * (the strictly lower part of the block, the Householder vectors, is kept),
+ * and U' and Vt go to DU(0:bi, k0:k0+bi) and DV(0:bi, k0:k0+bi). */
+static void diag_block(int n, double* A, int lda, int k0, int bi, double* DU, int lddu, double* DV, int lddv) {
+  double* M = (double*)xcalloc((size_t)bi * bi, sizeof(double));
+  double* J = (double*)xcalloc((size_t)bi * bi, sizeof(double));
+  double* sv = (double*)xcalloc((size_t)bi, sizeof(double));
+  for (int j = 0; j < bi; ++j)
+    for (int i = 0; i <= j; ++i) M[IX(j, i, bi)] = A[IX(k0 + i, k0 + j, lda)]; /* M = R11^T */
+  orc_jacobi_svd(bi, bi, M, bi, sv, J, bi);
+  double* Vt = DV + IX(0, k0, lddv);
+  double* Up = DU + IX(0, k0, lddu);
+  for (int j = 0; j < bi; ++j)
+    for (int i = 0; i < bi; ++i) Up[IX(i, j, lddu)] = J[IX(i, j, bi)];
+  for (int c = 0; c < bi; ++c) {
+    if (sv[c] > 0.0) {
+      for (int i = 0; i < bi; ++i) Vt[IX(i, c, lddv)] = M[IX(i, c, bi)] / sv[c];
+      continue;
+    }
+    for (int e = 0; e < bi; ++e) {
+      double* v = Vt + IX(0, c, lddv);
+      for (int i = 0; i < bi; ++i) v[i] = (i == e) ? 1.0 : 0.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < c; ++t) {
+          const double* u = Vt + IX(0, t, lddv);
+          double d = 0.0;
+          for (int i = 0; i < bi; ++i) d += u[i] * v[i];
+          for (int i = 0; i < bi; ++i) v[i] -= d * u[i];
+        }
+      double nv = 0.0;
+      for (int i = 0; i < bi; ++i) nv += v[i] * v[i];
+      nv = sqrt(nv);
+      if (nv > 0.5) {
+        for (int i = 0; i < bi; ++i) v[i] /= nv;
+        break;
+      }
+    }
+  }
+  /* A(0:k0, block) <- A(0:k0, block) Vt */
+  double* row = (double*)xcalloc((size_t)bi, sizeof(double));
+  for (int r = 0; r < k0; ++r) {
+    for (int j = 0; j < bi; ++j) {
+      double acc = 0.0;
+      for (int t = 0; t < bi; ++t) acc += A[IX(r, k0 + t, lda)] * Vt[IX(t, j, lddv)];
+      row[j] = acc;
+    }
+    for (int j = 0; j < bi; ++j) A[IX(r, k0 + j, lda)] = row[j];
+  }
+  /* R12 <- U'^T R12 (columns k0+bi..n-1) */
+  for (int col = k0 + bi; col < n; ++col) {
+    for (int i = 0; i < bi; ++i) {
+      double acc = 0.0;
+      for (int t = 0; t < bi; ++t) acc += Up[IX(t, i, lddu)] * A[IX(k0 + t, col, lda)];
+      row[i] = acc;
+    }
+    for (int i = 0; i < bi; ++i) A[IX(k0 + i, col, lda)] = row[i];
+  }
+  /* R11 <- D */
+  for (int j = 0; j < bi; ++j)
+    for (int i = 0; i <= j; ++i) A[IX(k0 + i, k0 + j, lda)] = (i == j) ? sv[j] : 0.0;
+  free(row);
+  free(M);
+  free(J);
+  free(sv);
+}
+
 int orc_rurv(int m, int n, double* A, int lda, int b, int p, int q, int k, const double* G, double* TU, int ldtu,
              double* WV, int ldwv, double* TV, int ldtv) {
+  return orc_rurv_diag(m, n, A, lda, b, p, q, k, G, TU, ldtu, WV, ldwv, TV, ldtv, NULL, 0, NULL, 0);
+}
+
+int orc_rurv_diag(int m, int n, double* A, int lda, int b, int p, int q, int k, const double* G, double* TU,
+                  int ldtu, double* WV, int ldwv, double* TV, int ldtv, double* DU, int lddu, double* DV, int lddv) {
   const int l = b + p;
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < b; ++i) { TU[IX(i, j, ldtu)] = 0.0; TV[IX(i, j, ldtv)] = 0.0; }
@@ -551,6 +628,7 @@ int orc_rurv(int m, int n, double* A, int lda, int b, int p, int q, int k, const
     double* Tb = TU + IX(0, k0, ldtu);
     orc_larft(mp, bi, X, lda, tau, Tb, ldtu);
     if (np > bi) orc_apply_block(mp, np - bi, bi, X, lda, Tb, ldtu, 1, A + IX(k0, k0 + bi, lda), lda);
+    if (DU && DV) diag_block(n, A, lda, k0, bi, DU, lddu, DV, lddv);
     free(tau);
     free(taus);
     free(Z);

@@ -95,6 +95,17 @@ int orc_rqrcp_ex(int m, int n, double* A, int lda, int b, int p, const double* G
 int orc_rurv(int m, int n, double* A, int lda, int b, int p, int q, int k, const double* G,
              double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv);
 
+/* orc_rurv with the diagonal blocks diagonalised (Sec. 6.2, Fig. blockRRQR,
+ * Method 3): after the left QR and trailing update of each block,
+ * R11 = U' D Vt^T (one-sided Jacobi), A(0:k0, block) <- A(0:k0, block) Vt,
+ * R12 <- U'^T R12, R11 <- D. U' and Vt (b_i x b_i) are stored at
+ * DU(0:b_i, k0:k0+b_i) and DV(0:b_i, k0:k0+b_i) (b x n each). Then
+ * A P = Q R with Q = prod_i H_i diag(I_k0, U'_i, I), P = prod_i S_i diag(I_k0, Vt_i, I).
+ * DU = DV = NULL is orc_rurv. */
+int orc_rurv_diag(int m, int n, double* A, int lda, int b, int p, int q, int k, const double* G,
+                  double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, double* DU, int lddu,
+                  double* DV, int lddv);
+
 /* One-sided Jacobi SVD (Hestenes 1958) of the r x c matrix M (overwritten by
  * M*J): on exit sv[c] holds the column norms of M*J sorted descending and J
  * (c x c, ldj) the matching right singular vectors. Returns the sweep count. */

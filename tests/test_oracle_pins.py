@@ -323,6 +323,63 @@ def test_rurv_factorization_and_eckart_young(q, p):
         assert np.linalg.norm(R[k:, k:]) >= np.sqrt(np.sum(s[k:] ** 2)) * (1 - 1e-9)
 
 
+def _blockdiag(D, n, b):
+    E = np.zeros((n, n))
+    for k0 in inputs.block_starts(n, b):
+        kb = min(b, n - k0)
+        E[k0:k0 + kb, k0:k0 + kb] = D[:kb, k0:k0 + kb]
+    return E
+
+
+@pytest.mark.parametrize("q,fam", [(0, "fast"), (1, "gauss"), (2, "fast")])
+def test_rurv_diag_blocks_are_svds(q, fam):
+    # Sec. 6.2 / Fig. blockRRQR: each diagonal block becomes D = diag(singular
+    # values of that block's R11), R11 = U' D Vt^T; the rest of the factorization
+    # (the trailing blocks) is that of the undiagonalised run, and
+    # A P = Q R holds with Q = Q_house blockdiag(U'), P = P_house blockdiag(Vt).
+    m, n, b, p = 120, 100, 24, 6
+    A = {"fast": inputs.a_fast, "gauss": inputs.a_gauss}[fam](n, seed=71 + q, m=m)
+    G = inputs.resample_blocks(72, m, n, b, p, full_last=True)
+    F, TU, WV, TV, DU, DV, done = oracle.rurv_diag(A, b, p, q, G)
+    F0, TU0, WV0, TV0, done0 = oracle.rurv(A, b, p, q, G)
+    assert done == done0 == n
+    R, R0 = np.triu(F)[:n], np.triu(F0)[:n]
+    Qh, Ph = _rurv_factors(F, TU, WV, TV, b)
+    E, Fd = _blockdiag(DU, n, b), _blockdiag(DV, n, b)
+    Q = Qh[:, :n] @ E
+    P = Ph @ Fd
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(A @ P - Q @ R) <= 1e-13 * nA
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= 1e-13
+    assert np.linalg.norm(P.T @ P - np.eye(n)) <= 1e-13
+    for k0 in inputs.block_starts(n, b):
+        k1 = min(n, k0 + b)
+        B = R[k0:k1, k0:k1]
+        d = np.diag(B)
+        assert np.all(B == np.diag(d))                     # exactly diagonal
+        assert np.all(d[:-1] >= d[1:]) and np.all(d >= 0)  # sorted, nonnegative
+        s0 = np.linalg.svd(R0[k0:k1, k0:k1], compute_uv=False)
+        np.testing.assert_allclose(d, s0, rtol=1e-12, atol=1e-14 * nA)
+        # the block row and the trailing block only turn by orthonormal factors
+        assert np.linalg.norm(R[k0:k1, k1:]) == pytest.approx(np.linalg.norm(R0[k0:k1, k1:]), rel=1e-12, abs=1e-14 * nA)
+        assert np.linalg.norm(R[k1:, k1:]) == pytest.approx(np.linalg.norm(R0[k1:, k1:]), rel=1e-12, abs=1e-14 * nA)
+
+
+def test_rurv_diag_rank_deficient_completes_vt():
+    # zero singular values: Vt is completed to an orthonormal matrix
+    m, n, b = 40, 30, 10
+    A = np.zeros((m, n), order="F")
+    A[:, 3] = 1.0
+    G = inputs.resample_blocks(5, m, n, b, 2, full_last=True)
+    F, TU, WV, TV, DU, DV, done = oracle.rurv_diag(A, b, 2, 1, G)
+    for k0 in inputs.block_starts(n, b):
+        kb = min(b, n - k0)
+        for X in (DU[:kb, k0:k0 + kb], DV[:kb, k0:k0 + kb]):
+            assert np.linalg.norm(X.T @ X - np.eye(kb)) <= 1e-13
+    R = np.triu(F)[:n]
+    assert abs(R[0, 0] - np.sqrt(m)) <= 1e-12 and np.linalg.norm(R) == pytest.approx(np.sqrt(m), rel=1e-13)
+
+
 def test_rurv_gap_gives_block_diagonal():
     # A = U diag(s) V^T with a 1e8 gap at a block boundary; with q = 2, p = b the
     # first block's S captures the top right singular space, so R12 is tiny.
