@@ -548,17 +548,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         uint32_t v[TC_EPI_COLS];
-        // slots 0, 1: |S| < 2^22 (one FADD each); slots 2..5: |S| < 2^24
+        // slots 0, 1: |S| < 2^22 (one FADD each); slots 2..5: |S| < 2^24. Slots
+        // (2k, 2k+1) are first combined in 32 bits, S_2k 2^7 + S_2k+1 < 2^31, so
+        // H takes three 64-bit shift-adds per window instead of six
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
+        for (int s = 0; s < 6; s += 2) {
+          int P[TC_EPI_COLS];
           tc_ld16(tbase + s * TC_BN, v);
           tc_wait_ld();
-          const float up = __uint_as_float((uint32_t)(127 + 7 * s) << 23);  // S_a = slot a x 2^(7a), exact
+          const float up0 = __uint_as_float((uint32_t)(127 + 7 * s) << 23);  // S_a = slot a x 2^(7a), exact
 #pragma unroll
           for (int c = 0; c < TC_EPI_COLS; ++c) {
-            const float f = __uint_as_float(v[c]) * up;
-            const int S = s < 2 ? small_float_to_int(f) : __float2int_rn(f);
-            H[c] += (long long)S << (7 * (5 - s));
+            const float f = __uint_as_float(v[c]) * up0;
+            P[c] = (s < 2 ? small_float_to_int(f) : __float2int_rn(f)) << 7;
+          }
+          tc_ld16(tbase + (s + 1) * TC_BN, v);
+          tc_wait_ld();
+          const float up1 = __uint_as_float((uint32_t)(127 + 7 * (s + 1)) << 23);
+#pragma unroll
+          for (int c = 0; c < TC_EPI_COLS; ++c) {
+            const float f = __uint_as_float(v[c]) * up1;
+            P[c] += s < 2 ? small_float_to_int(f) : __float2int_rn(f);
+            H[c] += (long long)P[c] << (7 * (4 - s));
           }
         }
 #pragma unroll
