@@ -95,8 +95,8 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
                  void* work, size_t lwork, int* info);
 
 /* Blocked QR with orthonormal pivoting A P = Q R, P = S_0 S_1 ... (Sec. 4.2,
- * 6.3, 6.4 without the diagonalisation of the diagonal blocks; Method 2 of Sec. 7,
- * and the power scheme of Method 3).
+ * 6.3, 6.4; Method 2 of Sec. 7, and with the power scheme and DU, DV given,
+ * Method 3 / Fig. blockRRQR with diagonalised diagonal blocks, Sec. 6.2).
  *   A        (device, in/out) m x n, ld lda: R above, left reflectors below.
  *   b, p, q  block size, over-sampling (l = b + p), power steps q >= 0.
  *   k        stop once k0 >= k (truncated rank-k URV); k <= 0 or k >= n: full.
@@ -106,10 +106,17 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
  *   WV       (device, out) n x n, ld ldwv: block i keeps the Householder vectors
  *            of S_i below the diagonal of WV(k0:n, k0:k0+b_i).
  *   TV       (device, out) b x n, ld ldtv: T of S_i per block.
+ *   DU, DV   (device, out, optional: both or neither) b x n, ld lddu / lddv >= b.
+ *            Given, each diagonal block is diagonalised after its left QR and
+ *            trailing update: R11 = U' D Vt^T (one-sided Jacobi), A(0:k0, block)
+ *            <- A(0:k0, block) Vt, R12 <- U'^T R12, R11 <- D (descending); U' is
+ *            stored at DU(0:b_i, k0:k0+b_i), Vt at DV(0:b_i, k0:k0+b_i). Then
+ *            Q = Q_house blockdiag(U'_i) and P = S_0 S_1 ... blockdiag(Vt_i).
  *   prec     RQR_FP64. */
 int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k,
                 uint64_t seed, const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV,
-                int ldtv, int prec, void* work, size_t lwork, int* info);
+                int ldtv, void* DU, int lddu, void* DV, int lddv, int prec, void* work, size_t lwork,
+                int* info);
 
 /* Forms the first `ncols` columns of Q = Q_0 Q_1 ... from the block reflectors
  * that a factor call left in F (m x n, ld ldf) and T (b x n, ld ldt).

@@ -221,6 +221,11 @@ bool gemm_f64x_tc(const Ctx& c, bool ta, bool tb, int M, int N, int K, double al
 // M J, sv the sorted norms, order the column order; flags: 2 ints of scratch.
 void jacobi_svd(const Ctx& c, int r, int cols, double* M, int ldm, double* J, int ldj, int nkeep, double* Js,
                 int ldjs, double* sv, int* order, int* flags);
+// Diagonalisation of a b_i x b_i block after jacobi_svd of M = R11^T (Sec. 6.2):
+// DU <- U' = Js, DV <- Vt (normalised columns of M in sorted order, completed
+// where a singular value is zero), upper triangle of F <- diag(sv).
+void diag_finish(const Ctx& c, int bi, const double* M, int ldm, const int* order, const double* sv, const double* Js,
+                 int ldjs, double* DU, int lddu, double* DV, int lddv, double* F, int ldf);
 // M (cols x kk) = R^T, R = upper triangle of the first kk rows of F.
 template <typename T>
 void r_transpose(const Ctx& c, int kk, int cols, const T* F, int ldf, T* M, int ldm);

@@ -412,8 +412,8 @@ void form_thin_q(const rqr::Ctx& c, int r, int cc, int kq, const double* F, int 
 }
 
 int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, int q, int k, uint64_t seed,
-              const double* G, double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, void* work,
-              size_t lwork, int* info) {
+              const double* G, double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, double* DU, int lddu,
+              double* DV, int lddv, void* work, size_t lwork, int* info) {
   using namespace rqr;
   const int l = b + p;
   Carver cv{static_cast<char*>(work), lwork, 0, false};
@@ -500,6 +500,26 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
       gemm<double>(c, true, false, bi, n2, mp, 1.0, w.Vx, mp, A2, lda, 0.0, w.W, bi, w.part, w.part_cap);
       gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
       gemm<double>(c, false, false, mp, n2, bi, -1.0, w.Vx, mp, w.W2, bi, 1.0, A2, lda, w.part, w.part_cap);
+    }
+    if (DU && DV) {
+      // Sec. 6.2 (Fig. blockRRQR): R11 = U' D Vt^T; A(0:k0, block) <- A(0:k0, block) Vt,
+      // R12 <- U'^T R12, R11 <- D
+      Phase ph(h, RQR_PHASE_PANEL, 6.0 * bi * (double)bi * bi + 2.0 * (k0 + n2) * (double)bi * bi);
+      r_transpose<double>(c, bi, bi, X, lda, w.Mj, bi);
+      jacobi_svd(c, bi, bi, w.Mj, bi, w.Jm, bi, bi, w.Js, bi, w.sv, w.order, w.flags);
+      double* Ub = DU + (size_t)k0 * lddu;
+      double* Vb = DV + (size_t)k0 * lddv;
+      diag_finish(c, bi, w.Mj, bi, w.order, w.sv, w.Js, bi, Ub, lddu, Vb, lddv, X, lda);
+      if (k0 > 0) {
+        double* Ab = A + (size_t)k0 * lda;
+        gemm<double>(c, false, false, k0, bi, bi, 1.0, Ab, lda, Vb, lddv, 0.0, w.P1, k0, w.part, w.part_cap);
+        copy_mat<double>(c, k0, bi, w.P1, k0, Ab, lda);
+      }
+      if (n2 > 0) {
+        double* R12 = A + k0 + (size_t)(k0 + bi) * lda;
+        gemm<double>(c, true, false, bi, n2, bi, 1.0, Ub, lddu, R12, lda, 0.0, w.W, bi, w.part, w.part_cap);
+        copy_mat<double>(c, bi, n2, w.W, bi, R12, lda);
+      }
     }
     k0 += bi;
     ++blk;
@@ -611,8 +631,8 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
 }
 
 int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k, uint64_t seed,
-                const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV, int ldtv, int prec, void* work,
-                size_t lwork, int* info) {
+                const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV, int ldtv, void* DU, int lddu,
+                void* DV, int lddv, int prec, void* work, size_t lwork, int* info) {
   if (!valid(h)) return -1;
   if (m < 0) return -2;
   if (n < 0 || n > m) return -3;
@@ -627,13 +647,16 @@ int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, in
   if (ldwv < std::max(1, n)) return -15;
   if (!TV && n > 0) return -16;
   if (ldtv < b) return -17;
-  if (prec != RQR_FP64) return -18;
-  if (!work && n > 0) return -19;
-  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -19;
+  if ((DU == nullptr) != (DV == nullptr)) return DU ? -20 : -18;
+  if (DU && lddu < b) return -19;
+  if (DV && lddv < b) return -21;
+  if (prec != RQR_FP64) return -22;
+  if (!work && n > 0) return -23;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -23;
   cudaGetLastError();
   return rurv_impl(h, m, n, static_cast<double*>(A), lda, b, p, q, k, seed, static_cast<const double*>(G),
                    static_cast<double*>(TU), ldtu, static_cast<double*>(WV), ldwv, static_cast<double*>(TV), ldtv,
-                   work, lwork, info);
+                   static_cast<double*>(DU), lddu, static_cast<double*>(DV), lddv, work, lwork, info);
 }
 
 int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt, void* Q, int ldq,

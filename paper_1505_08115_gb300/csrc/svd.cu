@@ -175,4 +175,83 @@ void jacobi_svd(const Ctx& c, int r, int cols, double* M, int ldm, double* J, in
   note_launch(c, 2);
 }
 
+// Finishes the diagonalisation of a b_i x b_i block (Sec. 6.2): with
+// M = R11^T J from jacobi_svd (unsorted columns), `order` and the sorted norms
+// sv, the right factor Vt(:, c) = M(:, order[c]) / sv[c]; a zero norm gets the
+// first unit vector that two Gram-Schmidt passes against the columns already set
+// leave with norm above 1/2. U' = Js is copied to DU, Vt to DV, and the upper
+// triangle of the block (F, ld ldf) becomes diag(sv). One CTA.
+__global__ void __launch_bounds__(256) k_diag_finish(int bi, const double* __restrict__ M, int ldm,
+                                                     const int* __restrict__ order, const double* __restrict__ sv,
+                                                     const double* __restrict__ Js, int ldjs, double* DU, int lddu,
+                                                     double* DV, int lddv, double* F, int ldf) {
+  __shared__ double red[8];
+  __shared__ double s_norm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < bi * bi; e += blockDim.x) {
+    const int i = e % bi, j = e / bi;
+    DU[i + (size_t)j * lddu] = Js[i + (size_t)j * ldjs];
+  }
+  for (int c = 0; c < bi; ++c) {
+    double* v = DV + (size_t)c * lddv;
+    const double s = sv[c];
+    if (s > 0.0) {
+      const double* mc = M + (size_t)order[c] * ldm;
+      for (int i = tid; i < bi; i += blockDim.x) v[i] = mc[i] / s;
+      __syncthreads();
+      continue;
+    }
+    for (int e = 0; e < bi; ++e) {
+      for (int i = tid; i < bi; i += blockDim.x) v[i] = (i == e) ? 1.0 : 0.0;
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < c; ++t) {
+          const double* u = DV + (size_t)t * lddv;
+          double d = 0.0;
+          for (int i = tid; i < bi; i += blockDim.x) d += u[i] * v[i];
+          d = warp_sum(d);
+          if (lane == 0) red[warp] = d;
+          __syncthreads();
+          if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+            s_norm = sum;
+          }
+          __syncthreads();
+          d = s_norm;
+          for (int i = tid; i < bi; i += blockDim.x) v[i] -= d * u[i];
+          __syncthreads();
+        }
+      double nv = 0.0;
+      for (int i = tid; i < bi; i += blockDim.x) nv += v[i] * v[i];
+      nv = warp_sum(nv);
+      if (lane == 0) red[warp] = nv;
+      __syncthreads();
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        s_norm = sqrt(sum);
+      }
+      __syncthreads();
+      nv = s_norm;
+      if (nv > 0.5) {
+        for (int i = tid; i < bi; i += blockDim.x) v[i] /= nv;
+        __syncthreads();
+        break;
+      }
+    }
+  }
+  for (int e = tid; e < bi * bi; e += blockDim.x) {
+    const int i = e % bi, j = e / bi;
+    if (i <= j) F[i + (size_t)j * ldf] = i == j ? sv[j] : 0.0;
+  }
+}
+
+void diag_finish(const Ctx& c, int bi, const double* M, int ldm, const int* order, const double* sv, const double* Js,
+                 int ldjs, double* DU, int lddu, double* DV, int lddv, double* F, int ldf) {
+  if (bi <= 0) return;
+  k_diag_finish<<<1, 256, 0, c.stream>>>(bi, M, ldm, order, sv, Js, ldjs, DU, lddu, DV, lddv, F, ldf);
+  note_launch(c);
+}
+
 }  // namespace rqr

@@ -59,7 +59,8 @@ def load(path: str = SO_PATH):
         L.rqr_set_stream.argtypes = [vp, vp]
         L.rqr_workspace_bytes.argtypes = [i, i, i, i, i, i, i, ctypes.POINTER(sz)]
         L.rqrcp_factor.argtypes = [vp, i, i, vp, i, i, i, u64, vp, i, vp, i, vp, i, i, vp, sz, ip]
-        L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, i, vp, sz, ip]
+        L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, vp, i, vp, i, i, vp, sz,
+                                  ip]
         L.rqr_form_q.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i, vp, sz]
         L.rqr_form_q_noalloc.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i]
         L.rqr_gemm.argtypes = [vp, i, i, i, i, i, i, ctypes.c_double, vp, i, vp, i, ctypes.c_double, vp, i, vp, sz]
@@ -175,24 +176,31 @@ def rqrcp_factor(A: torch.Tensor, b: int, p: int, seed: int = 1505, G: torch.Ten
 
 
 def rurv_factor(A: torch.Tensor, b: int, p: int, q: int, k: int = 0, seed: int = 1505,
-                G: torch.Tensor | None = None, work: torch.Tensor | None = None, check: bool = True):
-    """Blocked QR with orthonormal pivots. Returns (TU, WV, TV, info)."""
+                G: torch.Tensor | None = None, work: torch.Tensor | None = None, check: bool = True,
+                diag: bool = False):
+    """Blocked QR with orthonormal pivots. Returns (TU, WV, TV, info), or with
+    diag=True (diagonal blocks diagonalised, Sec. 6.2) (TU, WV, TV, DU, DV, info)."""
     _require_cuda(A)
     m, n = A.shape
     prec = _prec(A.dtype)
     TU = empty_colmajor(b, n, A.dtype, A.device)
     TV = empty_colmajor(b, n, A.dtype, A.device)
     WV = empty_colmajor(n, n, A.dtype, A.device)
+    DU = empty_colmajor(b, n, A.dtype, A.device) if diag else None
+    DV = empty_colmajor(b, n, A.dtype, A.device) if diag else None
     if work is None:
         work = torch.empty(workspace_bytes(m, n, b, p, q, prec), dtype=torch.uint8, device=A.device)
     info = ctypes.c_int(0)
     rc = load().rurv_factor(handle(A.device), m, n, _ptr(A), _ld(A), b, p, q, k, seed, _ptr(G), _ptr(TU), _ld(TU),
-                            _ptr(WV), _ld(WV), _ptr(TV), _ld(TV), prec, _ptr(work), work.numel(),
+                            _ptr(WV), _ld(WV), _ptr(TV), _ld(TV), _ptr(DU), _ld(DU) if diag else b, _ptr(DV),
+                            _ld(DV) if diag else b, prec, _ptr(work), work.numel(),
                             ctypes.byref(info) if check else None)
     if rc < 0:
         raise RQRError(f"rurv_factor: argument {-rc} invalid")
     if rc > 0:
         raise RQRError(f"rurv_factor: {STATUS.get(rc, rc)}")
+    if diag:
+        return TU, WV, TV, DU, DV, (info.value if check else None)
     return TU, WV, TV, (info.value if check else None)
 
 

@@ -121,3 +121,68 @@ def test_rurv_gap_block_diagonal():
     R = np.triu(host(Ad))[:n]
     assert np.linalg.norm(R[:b, b:]) <= 1e-12 * np.linalg.norm(R)
     np.testing.assert_allclose(np.linalg.svd(R[:b, :b], compute_uv=False), s[:b], rtol=1e-12)
+
+
+def _blockdiag(D, n, b):
+    E = np.zeros((n, n))
+    for k0 in inputs.block_starts(n, b):
+        kb = min(b, n - k0)
+        E[k0:k0 + kb, k0:k0 + kb] = D[:kb, k0:k0 + kb]
+    return E
+
+
+DIAG_CASES = [(160, 160, 32, 8, 1, "fast"), (200, 150, 32, 10, 2, "gauss"), (192, 192, 48, 16, 0, "fast")]
+
+
+@pytest.mark.parametrize("m,n,b,p,q,fam", DIAG_CASES)
+def test_rurv_diag_parity(m, n, b, p, q, fam):
+    """Diagonalised diagonal blocks (Sec. 6.2, Fig. blockRRQR): every diagonal
+    block of R is exactly diagonal with descending entries equal to the oracle's
+    (the singular values of that block), and A P = Q R with
+    Q = Q_house blockdiag(U'), P = P_house blockdiag(Vt) from the GPU's outputs."""
+    A = {"fast": inputs.a_fast, "gauss": inputs.a_gauss}[fam](n, seed=m + b + q + 1, m=m)
+    G = inputs.resample_blocks(78 + q, m, n, b, p, full_last=True)
+    F0, TU0, WV0, TV0, DU0, DV0, done0 = oracle.rurv_diag(A, b, p, q, G)
+    Ad = dev(A)
+    TU, WV, TV, DU, DV, info = rqr.rurv_factor(Ad, b, p, q, G=torch.from_numpy(G).cuda(), diag=True)
+    assert info == 0
+    F, TU, WV, TV, DU, DV = host(Ad), host(TU), host(WV), host(TV), host(DU), host(DV)
+    Qh, Ph = factors(F, TU, WV, TV, b)
+    Q = Qh[:, :n] @ _blockdiag(DU, n, b)
+    P = Ph @ _blockdiag(DV, n, b)
+    R = np.triu(F)[:n]
+    nA, nA2 = np.linalg.norm(A), np.linalg.norm(A, 2)
+    assert np.linalg.norm(A @ P - Q @ R) <= 1e-13 * nA
+    # U' = M v / sigma of a one-sided Jacobi SVD loses orthogonality in
+    # proportion to sigma_1 / sigma_j of the block, on both sides alike: the
+    # bound is twice the oracle's own loss, and at least 1e-13
+    Qh0, _ = factors(F0, TU0, WV0, TV0, b)
+    Q0 = Qh0[:, :n] @ _blockdiag(DU0, n, b)
+    orth0 = np.linalg.norm(Q0.T @ Q0 - np.eye(n))
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= max(1e-13, 2 * orth0)
+    assert np.linalg.norm(P.T @ P - np.eye(n)) <= 1e-13
+    R0 = np.triu(F0)[:n]
+    for k0 in inputs.block_starts(n, b):
+        k1 = min(n, k0 + b)
+        B = R[k0:k1, k0:k1]
+        d = np.diag(B)
+        assert np.all(B == np.diag(d))
+        assert np.all(d[:-1] >= d[1:]) and np.all(d >= 0)
+        assert np.abs(d - np.diag(R0[k0:k1, k0:k1])).max() <= 1e-9 * nA2
+
+
+def test_rurv_diag_rank_deficient():
+    m, n, b = 40, 30, 10
+    A = np.zeros((m, n), order="F")
+    A[:, 3] = 1.0
+    G = inputs.resample_blocks(5, m, n, b, 2, full_last=True)
+    Ad = dev(A)
+    TU, WV, TV, DU, DV, info = rqr.rurv_factor(Ad, b, 2, 1, G=torch.from_numpy(G).cuda(), diag=True)
+    assert info == 0
+    DU, DV, F = host(DU), host(DV), host(Ad)
+    for k0 in inputs.block_starts(n, b):
+        kb = min(b, n - k0)
+        for X in (DU[:kb, k0:k0 + kb], DV[:kb, k0:k0 + kb]):
+            assert np.linalg.norm(X.T @ X - np.eye(kb)) <= 1e-13
+    R = np.triu(F)[:n]
+    assert abs(R[0, 0] - np.sqrt(m)) <= 1e-12 and abs(np.linalg.norm(R) - np.sqrt(m)) <= 1e-12
