@@ -33,6 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GFLOP/s & roofline fraction of randomized QRCP at n=16384 vs FP64 GPU, fixed residual"
+# DRAM bytes (read + write) over algorithmic bytes of one k_oztc launch, from
+# an ncu capture of the current kernel: 537.2 MB measured against 591.2 MB
+# (C read and written once plus both operands' digit planes)
+K_OZTC_DRAM_OVER_ALGORITHMIC = 0.909
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0  # GB300 dense nominal FP64 / bf16 ratio
 
 
@@ -329,7 +333,10 @@ def main():
                 "launches_per_step": kern["launches"] // a.steps, "ms_per_step": kern["ms"] / a.steps,
                 "algorithmic_bytes_per_launch": kern["bytes"] / max(kern["launches"], 1),
                 "fp64_equivalent_tflops": achieved / 36.0, "update_phase_fp64_equivalent_tflops": fp64_eq,
-                "traffic": None}
+                "traffic": K_OZTC_DRAM_OVER_ALGORITHMIC * kern["bytes"] / max(kern["launches"], 1),
+                "traffic_basis": (f"ncu dram__bytes_read+write of one k_oztc trailing update (M 6016, N 5888, "
+                                  f"K 128) = {K_OZTC_DRAM_OVER_ALGORITHMIC} x its algorithmic bytes, "
+                                  f"times this run's mean algorithmic bytes per launch")}
     else:
         peak = pk["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
         roof = {"kernel": "trailing update (k_dgemm, mma.sync.m8n8k4.f64)", "bound": "tensor",
