@@ -108,8 +108,9 @@ template <typename T>
 __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int l = a.l, C = gridDim.x;
-  T* tile = reinterpret_cast<T*>(smem_raw);  // [per][l]
-  T* v = tile + (size_t)a.per * l;            // [l]
+  const int LS = l | 1;                       // odd column stride: a thread per column reads without bank conflicts
+  T* tile = reinterpret_cast<T*>(smem_raw);  // [per][LS]
+  T* v = tile + (size_t)a.per * LS;           // [l]
   T* nrm = v + l;                             // [per] squared norm of rows s.. of each column
   T* ref = nrm + a.per;                       // [per] the last exactly computed squared norm
   const int LB = l + 2;                       // colbuf stride: values, norm, reference
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   const int lo = q * a.per, hi = min(a.np, lo + a.per), cnt = max(0, hi - lo);
   for (int e = tid; e < cnt * l; e += PT) {
     const int pl = e / l, r = e % l;
-    tile[e] = a.Y[(size_t)(lo + pl) * a.ldy + r];
+    tile[(size_t)pl * LS + r] = a.Y[(size_t)(lo + pl) * a.ldy + r];
   }
   __syncthreads();
   // full column norms, warp candidates
   T wn = T(-1);
   int wp = 0x7fffffff;
   for (int pl = warp; pl < cnt; pl += PNW) {
-    const T* y = tile + (size_t)pl * l;
+    const T* y = tile + (size_t)pl * LS;
     T ss = T(0);
     for (int r = lane; r < l; r += 32) ss += y[r] * y[r];
     ss = warp_sum(ss);
@@ -144,6 +145,15 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   for (int s = 0; s < a.bsteps; ++s) {
     const int par = s & 1;
     // ---- publish the CTA candidate and, if owned, the column at position s
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T n2 = __shfl_xor_sync(0xffffffffu, wn, o);
+      const int p2 = __shfl_xor_sync(0xffffffffu, wp, o);
+      if (better(n2, p2, wn, wp)) {
+        wn = n2;
+        wp = p2;
+      }
+    }
     if (lane == 0) {
       shn[warp] = wn;
       shp[warp] = wp;
@@ -161,9 +171,9 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       a.cand_p[par * C + q] = bp;
     }
     if (bp >= lo && bp < hi)
-      for (int r = s + tid; r < l; r += PT) a.candcol[((size_t)par * C + q) * l + r] = tile[(size_t)(bp - lo) * l + r];
+      for (int r = s + tid; r < l; r += PT) a.candcol[((size_t)par * C + q) * l + r] = tile[(size_t)(bp - lo) * LS + r];
     if (s >= lo && s < hi) {
-      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * LB + r] = tile[(size_t)(s - lo) * l + r];
+      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * LB + r] = tile[(size_t)(s - lo) * LS + r];
       if (tid == 0) {
         a.colbuf[(size_t)par * LB + l] = nrm[s - lo];
         a.colbuf[(size_t)par * LB + l + 1] = ref[s - lo];
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     } else if (pw != s && pw >= lo && pw < hi) {
       // the column that was at position s moves to the winner's position
       for (int r = s + tid - 32; r < l; r += PT - 32)
-        tile[(size_t)(pw - lo) * l + r] = __ldcg(a.colbuf + (size_t)par * LB + r);
+        tile[(size_t)(pw - lo) * LS + r] = __ldcg(a.colbuf + (size_t)par * LB + r);
       if (tid == 32) {
         nrm[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l);
         ref[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l + 1);
@@ -250,36 +260,57 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     __syncthreads();
     if (s + 1 >= a.bsteps) break;
     // ---- apply the reflector to the remaining columns, norms of rows s+1..
+    // One thread per column: the FP64 pipe issues a warp instruction for 32
+    // columns at once, with no shuffles or idle lanes on the short columns of
+    // the late steps. A column whose downdated norm lost too many digits gets
+    // its exact norm from the whole warp afterwards.
     const T tau = s_tau;
     wn = T(-1);
     wp = 0x7fffffff;
-    for (int pl = max(0, s + 1 - lo) + warp; pl < cnt; pl += PNW) {
-      T* y = tile + (size_t)pl * l + s;
-      T dot = T(0);
-      for (int r = lane; r < L; r += 32) dot += v[r] * y[r];
-      dot = warp_sum(dot) * tau;
-      T y0 = T(0);
-      for (int r = lane; r < L; r += 32) {
-        const T nx = y[r] - dot * v[r];
-        y[r] = nx;
-        if (r == 0) y0 = nx;
-      }
-      y0 = __shfl_sync(0xffffffffu, y0, 0);
-      const T rf = ref[pl];
-      T nn = nrm[pl] - y0 * y0;
-      if (!(nn > kRecompute * rf)) {
-        // exact squared norm of rows s+1.. (the downdate lost too many digits)
-        __syncwarp();
-        T ss = T(0);
-        for (int r = 1 + lane; r < L; r += 32) ss += y[r] * y[r];
-        nn = warp_sum(ss);
-        if (lane == 0) ref[pl] = nn;
+    for (int base = max(0, s + 1 - lo); base < cnt; base += PT) {
+      const int pl = base + tid;
+      const bool act = pl < cnt;
+      T nn = T(-1);
+      bool redo = false;
+      if (act) {
+        T* y = tile + (size_t)pl * LS + s;
+        T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+        int r = 0;
+        for (; r + 4 <= L; r += 4) {
+          d0 += v[r] * y[r];
+          d1 += v[r + 1] * y[r + 1];
+          d2 += v[r + 2] * y[r + 2];
+          d3 += v[r + 3] * y[r + 3];
+        }
+        for (; r < L; ++r) d0 += v[r] * y[r];
+        const T dot = ((d0 + d1) + (d2 + d3)) * tau;
+        for (r = 0; r < L; ++r) y[r] -= dot * v[r];
+        const T y0 = y[0];
+        nn = nrm[pl] - y0 * y0;
+        redo = !(nn > kRecompute * ref[pl]);
       }
       __syncwarp();
-      if (lane == 0) nrm[pl] = nn;
-      if (better(nn, lo + pl, wn, wp)) {
-        wn = nn;
-        wp = lo + pl;
+      unsigned m = __ballot_sync(0xffffffffu, redo);
+      while (m) {
+        // exact squared norm of rows s+1.. of the lane's column
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int pc = base + (tid & ~31) + src;
+        const T* y = tile + (size_t)pc * LS + s;
+        T ss = T(0);
+        for (int r = 1 + lane; r < L; r += 32) ss += y[r] * y[r];
+        ss = warp_sum(ss);
+        if (lane == src) {
+          nn = ss;
+          ref[pc] = ss;
+        }
+      }
+      if (act) {
+        nrm[pl] = nn;
+        if (better(nn, lo + pl, wn, wp)) {
+          wn = nn;
+          wp = lo + pl;
+        }
       }
     }
   }
@@ -337,16 +368,17 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = a.nc, R = a.R, C = gridDim.x;
   T* w = reinterpret_cast<T*>(smem_raw);  // [nc]
-  T* tile = w + nc;                       // [nc][R]: tile[c * R + rr] = P(r0 + rr, c)
+  T* tile = w + nc;                       // [nc][RS]: tile[c * RS + rr] = P(r0 + rr, c)
   __shared__ T wsum[PT / 32];
   __shared__ T s_coef[NCOEF];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int RS = R | 1;  // odd column stride: a thread per column reads without bank conflicts
   const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
   T* total = a.coef;  // [nc + 1]
   unsigned nbar = 0;
   for (int e = tid; e < nr * nc; e += PT) {
     const int rr = e % nr, cc = e / nr;
-    tile[cc * R + rr] = a.P[r0 + rr + (size_t)cc * a.ldp];
+    tile[(size_t)cc * RS + rr] = a.P[r0 + rr + (size_t)cc * a.ldp];
   }
   __syncthreads();
   // Exchange after the partials of column jn are published: totals, then the
@@ -375,19 +407,19 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     for (int c = 1 + warp; c < nc; c += PT / 32) {
       T acc = T(0);
       for (int rr = lane; rr < nr; rr += 32)
-        if (r0 + rr > 0) acc += tile[rr] * tile[(size_t)c * R + rr];
+        if (r0 + rr > 0) acc += tile[rr] * tile[(size_t)c * RS + rr];
       acc = warp_sum(acc);
       if (lane == 0) myp[1 + c] = acc;
     }
     if (r0 == 0 && nr > 0)
-      for (int c = tid; c < nc; c += PT) a.rowbuf[c] = tile[(size_t)c * R];
+      for (int c = tid; c < nc; c += PT) a.rowbuf[c] = tile[(size_t)c * RS];
     if (!exchange(0)) return;
   }
   for (int j = 0; j < nc; ++j) {
     const T tauj = s_coef[0], beta = s_coef[1], d = s_coef[2];
     const bool has = s_coef[3] != T(0);
     const int lo = min(nr, max(0, j - r0));
-    T* tj = tile + (size_t)j * R;
+    T* tj = tile + (size_t)j * RS;
     for (int rr = lo + tid; rr < nr; rr += PT) {
       const int i = r0 + rr;
       if (i > j) {
@@ -398,7 +430,7 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     }
     __syncthreads();
     if (j + 1 >= nc) break;
-    T* t1 = tile + (size_t)(j + 1) * R;
+    T* t1 = tile + (size_t)(j + 1) * RS;
     const T w1 = w[j + 1];
     for (int rr = lo + tid; rr < nr; rr += PT) {
       const int i = r0 + rr;
@@ -411,29 +443,45 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       if (r0 + rr > j + 1) ssum += t1[rr] * t1[rr];
     ssum = block_sum(ssum, wsum);
     if (tid == 0) myp[0] = ssum;
-    for (int c = j + 2 + warp; c < nc; c += PT / 32) {
-      T* x = tile + (size_t)c * R;
+    // one thread per later column: the FP64 pipe issues each warp
+    // instruction for 32 columns, with no shuffle reduction per column
+    for (int c = j + 2 + tid; c < nc; c += PT) {
+      T* x = tile + (size_t)c * RS;
       const T wc = w[c];
-      T acc = T(0);
-      for (int rr = lo + lane; rr < nr; rr += 32) {
-        const int i = r0 + rr;
-        const T xv = x[rr] - wc * (i == j ? T(1) : tj[rr]);
-        x[rr] = xv;
-        if (i > j + 1) acc += t1[rr] * xv;
+      int rr = lo;
+      if (rr < nr && r0 + rr == j) {  // row j: the reflector's implicit unit entry
+        x[rr] -= wc;
+        ++rr;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) myp[1 + c] = acc;
+      if (rr < nr && r0 + rr == j + 1) {  // row j+1: updated, not in the dot product
+        x[rr] -= wc * tj[rr];
+        ++rr;
+      }
+      T acc0 = T(0), acc1 = T(0);
+      for (; rr + 2 <= nr; rr += 2) {
+        const T x0 = x[rr] - wc * tj[rr], x1 = x[rr + 1] - wc * tj[rr + 1];
+        x[rr] = x0;
+        x[rr + 1] = x1;
+        acc0 += t1[rr] * x0;
+        acc1 += t1[rr + 1] * x1;
+      }
+      if (rr < nr) {
+        const T x0 = x[rr] - wc * tj[rr];
+        x[rr] = x0;
+        acc0 += t1[rr] * x0;
+      }
+      myp[1 + c] = acc0 + acc1;
     }
     __syncthreads();  // row j+1 of every column is final before it is published
     T* rb = a.rowbuf + (size_t)((j + 1) & 1) * nc;
     if (j + 1 >= r0 && j + 1 < r1)
-      for (int c = j + 1 + tid; c < nc; c += PT) rb[c] = tile[(size_t)c * R + (j + 1 - r0)];
+      for (int c = j + 1 + tid; c < nc; c += PT) rb[c] = tile[(size_t)c * RS + (j + 1 - r0)];
     if (!exchange(j + 1)) return;
   }
   __syncthreads();
   for (int e = tid; e < nr * nc; e += PT) {
     const int rr = e % nr, cc = e / nr;
-    a.P[r0 + rr + (size_t)cc * a.ldp] = tile[cc * R + rr];
+    a.P[r0 + rr + (size_t)cc * a.ldp] = tile[(size_t)cc * RS + rr];
   }
 }
 
@@ -445,7 +493,7 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
 template <typename T>
 bool panel_qr_persist(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch, int C, int R) {
   if (mp <= 0 || nc <= 0) return true;
-  const size_t smem = sizeof(T) * ((size_t)nc + (size_t)nc * R);
+  const size_t smem = sizeof(T) * ((size_t)nc + (size_t)nc * (R | 1));
   if (smem > 200 * 1024 || C > c.sms) return false;
   static int attr_set = 0;
   if (!attr_set) {
@@ -484,7 +532,7 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
   C = std::max(1, std::min(sms, ceil_div(np, 8)));
   per = ceil_div(std::max(np, 1), C);
   C = ceil_div(std::max(np, 1), per);
-  return sizeof(double) * ((size_t)per * l + l + 2 * (size_t)per);
+  return sizeof(double) * ((size_t)per * (l | 1) + l + 2 * (size_t)per);
 }
 
 size_t ypick_persist_scratch_bytes(int l, int np, int sms) {
