@@ -355,6 +355,53 @@ __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__
   }
 }
 
+// T as the inverse of S = diag(1/tau) + striu(V^T V): S has the same
+// column recursion as T (Sec. 5.1), so S T = I. Column j of T is then one
+// back substitution, x_j = tau_j and x_i = -tau_i sum_{k=i+1..j} G_ik x_k,
+// independent of the other columns: one warp per column, all columns at once.
+// Lane l keeps the running sums of rows l, l + 32, ...; G's strict upper
+// triangle up to column j sits packed in shared memory (column k at
+// k (k - 1) / 2). A zero tau_i (no reflector) gives a zero row and column,
+// as in the recursion.
+constexpr int kLarftRows = 8;  // rows per lane: kb <= 256
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_larft_inv(int kb, const T* __restrict__ gram, int ldg, const T* __restrict__ tau,
+                                                  T* Tm, int ldt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ts = reinterpret_cast<T*>(smem_raw);  // [kb] tau
+  T* Gp = ts + kb;                         // packed strict upper triangle, columns 1..j
+  const int j = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < kb; i += 32) ts[i] = tau[i];
+  for (int k = 1; k <= j; ++k)
+    for (int i = lane; i < k; i += 32) Gp[(size_t)k * (k - 1) / 2 + i] = gram[i + (size_t)k * ldg];
+  __syncwarp();
+  T acc[kLarftRows];
+#pragma unroll
+  for (int r = 0; r < kLarftRows; ++r) acc[r] = T(0);
+  T* tcol = Tm + (size_t)j * ldt;
+  T xk = ts[j];  // x_j
+  if (lane == 0) tcol[j] = xk;
+  for (int i = j + 1 + lane; i < kb; i += 32) tcol[i] = T(0);
+  for (int k = j; k >= 1; --k) {
+    // add column k of G times x_k to the rows above k, then finish row k - 1
+    const T* gk = Gp + (size_t)k * (k - 1) / 2;
+#pragma unroll
+    for (int r = 0; r < kLarftRows; ++r) {
+      const int i = lane + 32 * r;
+      if (32 * r < k && i < k) acc[r] += gk[i] * xk;
+    }
+    const int o = k - 1, orow = o >> 5;
+    T a = acc[0];
+#pragma unroll
+    for (int r = 1; r < kLarftRows; ++r)
+      if (r == orow) a = acc[r];
+    a = __shfl_sync(0xffffffffu, a, o & 31);
+    xk = -ts[o] * a;
+    if (lane == (o & 31)) tcol[o] = xk;
+  }
+}
+
 // Gram matrix of V = E + L from the Gram matrix of its strictly lower part:
 // V^T V = L^T L + I + L1 + L1^T, L1 = the top kb x kb block of L.
 template <typename T>
@@ -511,6 +558,14 @@ void qrcp_block(const Ctx& c, int m, int r0, int c0, int nc, T* A, int lda, int3
 template <typename T>
 void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm, int ldt) {
   if (kb <= 0) return;
+  // column-parallel back substitution while G's triangle fits in shared memory
+  const size_t inv_sm = sizeof(T) * ((size_t)kb + (size_t)kb * (kb - 1) / 2);
+  if (kb <= 32 * kLarftRows && inv_sm <= 200 * 1024) {
+    if (inv_sm > 48 * 1024) cudaFuncSetAttribute(k_larft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_sm);
+    k_larft_inv<T><<<kb, 32, inv_sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt);
+    note_launch(c);
+    return;
+  }
   const size_t need = sizeof(T) * (size_t)kb * kb;
   const int use_smem = need <= 200 * 1024 ? 1 : 0;
   const size_t sm = use_smem ? need : 0;

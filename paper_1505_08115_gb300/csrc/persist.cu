@@ -79,7 +79,7 @@ struct PArgs {
   const T* Y;
   int ldy;
   int* picks;
-  T* cand_n;    // [2][C] candidate squared norms (step parity)
+  long long* cand_k;  // [2][C] candidate keys (step parity)
   int* cand_p;  // [2][C] candidate positions
   T* candcol;   // [2][C][l] candidate columns
   T* colbuf;    // [2][l + 2] column leaving the pivot position, its norm and reference norm
@@ -87,10 +87,20 @@ struct PArgs {
   int* status;
 };
 
+// Candidates compare by key: the bit pattern of a squared norm (>= 0) as a
+// signed integer orders like the norm itself, and anything else (the empty
+// candidate, NaN) gets -1. The comparisons then run on the integer pipe; as
+// FP64 compares, every thread of every CTA spent ~20 clocks of the SM's FP64
+// pipe on each of them per step.
+// (-0.0 gets the key of +0.0.)
+__device__ __forceinline__ long long norm_key(double n) {
+  return n >= 0.0 ? (__double_as_longlong(n) & 0x7fffffffffffffffll) : -1ll;
+}
+__device__ __forceinline__ long long norm_key(float n) { return n >= 0.f ? (long long)(__float_as_int(n) & 0x7fffffff) : -1ll; }
+
 // Better candidate: larger squared norm, lower position on ties.
-template <typename T>
-__device__ __forceinline__ bool better(T n, int p, T bn, int bp) {
-  return n > bn || (n == bn && p < bp);
+__device__ __forceinline__ bool better(long long k, int p, long long bk, int bp) {
+  return k > bk || (k == bk && p < bp);
 }
 
 // b steps of Fig. QR on the sketch. Per step s every CTA publishes its best
@@ -114,7 +124,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   T* nrm = v + l;                             // [per] squared norm of rows s.. of each column
   T* ref = nrm + a.per;                       // [per] the last exactly computed squared norm
   const int LB = l + 2;                       // colbuf stride: values, norm, reference
-  __shared__ T shn[PNW];
+  __shared__ long long shn[PNW];
   __shared__ int shp[PNW], shq[PNW];
   __shared__ T s_tau;
   __shared__ int s_win, s_pos;
@@ -126,7 +136,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   }
   __syncthreads();
   // full column norms, warp candidates
-  T wn = T(-1);
+  long long wn = -1;
   int wp = 0x7fffffff;
   for (int pl = warp; pl < cnt; pl += PNW) {
     const T* y = tile + (size_t)pl * LS;
@@ -137,8 +147,8 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       nrm[pl] = ss;
       ref[pl] = ss;
     }
-    if (better(ss, lo + pl, wn, wp)) {
-      wn = ss;
+    if (better(norm_key(ss), lo + pl, wn, wp)) {
+      wn = norm_key(ss);
       wp = lo + pl;
     }
   }
@@ -147,7 +157,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     // ---- publish the CTA candidate and, if owned, the column at position s
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const T n2 = __shfl_xor_sync(0xffffffffu, wn, o);
+      const long long n2 = __shfl_xor_sync(0xffffffffu, wn, o);
       const int p2 = __shfl_xor_sync(0xffffffffu, wp, o);
       if (better(n2, p2, wn, wp)) {
         wn = n2;
@@ -159,7 +169,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       shp[warp] = wp;
     }
     __syncthreads();
-    T bn = T(-1);
+    long long bn = -1;
     int bp = 0x7fffffff;
     for (int w = 0; w < PNW; ++w)
       if (better(shn[w], shp[w], bn, bp)) {
@@ -167,7 +177,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
         bp = shp[w];
       }
     if (tid == 0) {
-      a.cand_n[par * C + q] = bn;
+      a.cand_k[par * C + q] = bn;
       a.cand_p[par * C + q] = bp;
     }
     if (bp >= lo && bp < hi)
@@ -181,10 +191,10 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     }
     if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status)) return;
     // ---- global winner (every CTA, identical order)
-    T cn = T(-1);
+    long long cn = -1;
     int cp = 0x7fffffff, cq = 0;
     for (int t = tid; t < C; t += PT) {
-      const T n = __ldcg(a.cand_n + par * C + t);
+      const long long n = __ldcg(a.cand_k + par * C + t);
       const int pp = __ldcg(a.cand_p + par * C + t);
       if (better(n, pp, cn, cp)) {
         cn = n;
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const T n2 = __shfl_xor_sync(0xffffffffu, cn, o);
+      const long long n2 = __shfl_xor_sync(0xffffffffu, cn, o);
       const int p2 = __shfl_xor_sync(0xffffffffu, cp, o);
       const int q2 = __shfl_xor_sync(0xffffffffu, cq, o);
       if (better(n2, p2, cn, cp)) {
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     }
     __syncthreads();
     if (tid == 0) {
-      T gn = shn[0];
+      long long gn = shn[0];
       int gp = shp[0], gq = shq[0];
       for (int w = 1; w < PNW; ++w)
         if (better(shn[w], shp[w], gn, gp)) {
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     // the late steps. A column whose downdated norm lost too many digits gets
     // its exact norm from the whole warp afterwards.
     const T tau = s_tau;
-    wn = T(-1);
+    wn = -1;
     wp = 0x7fffffff;
     for (int base = max(0, s + 1 - lo); base < cnt; base += PT) {
       const int pl = base + tid;
@@ -307,8 +317,9 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       }
       if (act) {
         nrm[pl] = nn;
-        if (better(nn, lo + pl, wn, wp)) {
-          wn = nn;
+        const long long key = norm_key(nn);
+        if (better(key, lo + pl, wn, wp)) {
+          wn = key;
           wp = lo + pl;
         }
       }
@@ -438,11 +449,18 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     }
     __syncthreads();
     T* myp = a.part + (size_t)q * (nc + 1);
-    T ssum = T(0);
-    for (int rr = lo + tid; rr < nr; rr += PT)
-      if (r0 + rr > j + 1) ssum += t1[rr] * t1[rr];
-    ssum = block_sum(ssum, wsum);
-    if (tid == 0) myp[0] = ssum;
+    if (tid == PT - 1) {
+      // squared norm of column j+1 below the diagonal, in the last thread
+      // (idle in the column loop below unless nc > PT + j + 1)
+      T s0 = T(0), s1 = T(0);
+      int rr = max(lo, j + 2 - r0);
+      for (; rr + 2 <= nr; rr += 2) {
+        s0 += t1[rr] * t1[rr];
+        s1 += t1[rr + 1] * t1[rr + 1];
+      }
+      if (rr < nr) s0 += t1[rr] * t1[rr];
+      myp[0] = s0 + s1;
+    }
     // one thread per later column: the FP64 pipe issues each warp
     // instruction for 32 columns, with no shuffle reduction per column
     for (int c = j + 2 + tid; c < nc; c += PT) {
@@ -564,12 +582,12 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
   char* p = static_cast<char*>(scratch);
   GridSync* gs = reinterpret_cast<GridSync*>(p);
   p += 64;
-  T* cand_n = reinterpret_cast<T*>(p);
-  T* candcol = cand_n + 2 * (size_t)C;
+  long long* cand_k = reinterpret_cast<long long*>(p);
+  T* candcol = reinterpret_cast<T*>(cand_k + 2 * (size_t)C);
   T* colbuf = candcol + 2 * (size_t)C * l;
   int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)(l + 2) + 8);
   cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_n, cand_p, candcol, colbuf, gs, c.status};
+  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_k, cand_p, candcol, colbuf, gs, c.status};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_ypick_persist<T>, dim3(C), dim3(PT), args, smem, c.stream) !=
       cudaSuccess) {
