@@ -358,24 +358,46 @@ __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__
 // T as the inverse of S = diag(1/tau) + striu(V^T V): S has the same
 // column recursion as T (Sec. 5.1), so S T = I. Column j of T is then one
 // back substitution, x_j = tau_j and x_i = -tau_i sum_{k=i+1..j} G_ik x_k,
-// independent of the other columns: one warp per column, all columns at once.
-// Lane l keeps the running sums of rows l, l + 32, ...; G's strict upper
-// triangle up to column j sits packed in shared memory (column k at
-// k (k - 1) / 2). A zero tau_i (no reflector) gives a zero row and column,
-// as in the recursion.
+// independent of the other columns: one CTA per column, all columns at once.
+// The CTA's threads copy G's strict upper triangle up to column j into
+// shared memory, packed (column k at k (k - 1) / 2), eight independent loads
+// per thread at a time; one warp then runs the substitution, lane l keeping
+// the running sums of rows l, l + 32, .... A zero tau_i (no reflector) gives
+// a zero row and column, as in the recursion.
 constexpr int kLarftRows = 8;  // rows per lane: kb <= 256
+constexpr int kLarftT = 256;   // threads per CTA for the copy
+constexpr int kLarftU = 8;     // loads in flight per thread
 
 template <typename T>
-__global__ void __launch_bounds__(32) k_larft_inv(int kb, const T* __restrict__ gram, int ldg, const T* __restrict__ tau,
-                                                  T* Tm, int ldt) {
+__global__ void __launch_bounds__(kLarftT) k_larft_inv(int kb, const T* __restrict__ gram, int ldg,
+                                                       const T* __restrict__ tau, T* Tm, int ldt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ts = reinterpret_cast<T*>(smem_raw);  // [kb] tau
   T* Gp = ts + kb;                         // packed strict upper triangle, columns 1..j
-  const int j = blockIdx.x, lane = threadIdx.x;
-  for (int i = lane; i < kb; i += 32) ts[i] = tau[i];
-  for (int k = 1; k <= j; ++k)
-    for (int i = lane; i < k; i += 32) Gp[(size_t)k * (k - 1) / 2 + i] = gram[i + (size_t)k * ldg];
-  __syncwarp();
+  const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < kb; i += kLarftT) ts[i] = tau[i];
+  const int tot = j * (j + 1) / 2;  // entries of columns 1..j
+  for (int e0 = tid; e0 < tot; e0 += kLarftT * kLarftU) {
+    T v[kLarftU];
+#pragma unroll
+    for (int u = 0; u < kLarftU; ++u) {
+      const int e = e0 + u * kLarftT;
+      if (e < tot) {
+        // column k = the largest k with k (k - 1) / 2 <= e, row i = the rest
+        int k = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+        if (k * (k - 1) / 2 > e) --k;
+        if ((k + 1) * k / 2 <= e) ++k;
+        v[u] = gram[(e - k * (k - 1) / 2) + (size_t)k * ldg];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLarftU; ++u) {
+      const int e = e0 + u * kLarftT;
+      if (e < tot) Gp[e] = v[u];
+    }
+  }
+  __syncthreads();
+  if (tid >= 32) return;
   T acc[kLarftRows];
 #pragma unroll
   for (int r = 0; r < kLarftRows; ++r) acc[r] = T(0);
@@ -562,7 +584,7 @@ void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm
   const size_t inv_sm = sizeof(T) * ((size_t)kb + (size_t)kb * (kb - 1) / 2);
   if (kb <= 32 * kLarftRows && inv_sm <= 200 * 1024) {
     if (inv_sm > 48 * 1024) cudaFuncSetAttribute(k_larft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_sm);
-    k_larft_inv<T><<<kb, 32, inv_sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt);
+    k_larft_inv<T><<<kb, kLarftT, inv_sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt);
     note_launch(c);
     return;
   }

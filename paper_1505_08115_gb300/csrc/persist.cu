@@ -353,14 +353,15 @@ template <typename T>
 __device__ __forceinline__ void reduce_entry(int e, int nc, const T* part, T* total) {
   __shared__ T wsum[pnl::PT / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, C = gridDim.x;
+  const int nw = min(pnl::PT / 32, (C + 31) / 32);  // warps holding partials
   T x = T(0);
   for (int q = tid; q < C; q += pnl::PT) x += __ldcg(part + (size_t)q * (nc + 1) + e);
-  x = warp_sum(x);
+  if (warp < nw) x = warp_sum(x);
   if (lane == 0) wsum[warp] = x;
   __syncthreads();
   if (tid == 0) {
     T t = T(0);
-    for (int w = 0; w < pnl::PT / 32; ++w) t += wsum[w];
+    for (int w = 0; w < nw; ++w) t += wsum[w];
     total[e] = t;
   }
   __syncthreads();
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   T* tile = w + nc;                       // [nc][RS]: tile[c * RS + rr] = P(r0 + rr, c)
   __shared__ T wsum[PT / 32];
   __shared__ T s_coef[NCOEF];
+  __shared__ T s_rd;  // 1 / d of the current reflector: one division per column, not one per row
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int RS = R | 1;  // odd column stride: a thread per column reads without bank conflicts
   const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
@@ -400,10 +402,13 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       if (e == 0 || e >= jn + 2) reduce_entry<T>(e, nc, a.part, total);
     if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status)) return false;
     const T* rb = a.rowbuf + (size_t)(jn & 1) * nc;
-    if (tid == 0) reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
+    if (tid == 0) {
+      reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
+      s_rd = T(1) / s_coef[2];
+    }
     __syncthreads();
-    const T tau = s_coef[0], d = s_coef[2];
-    for (int c = tid; c < nc; c += PT) w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) / d) : T(0);
+    const T tau = s_coef[0], rd = s_rd;
+    for (int c = tid; c < nc; c += PT) w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) * rd) : T(0);
     __syncthreads();
     return true;
   };
@@ -427,14 +432,14 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     if (!exchange(0)) return;
   }
   for (int j = 0; j < nc; ++j) {
-    const T tauj = s_coef[0], beta = s_coef[1], d = s_coef[2];
+    const T tauj = s_coef[0], beta = s_coef[1], rd = s_rd;
     const bool has = s_coef[3] != T(0);
     const int lo = min(nr, max(0, j - r0));
     T* tj = tile + (size_t)j * RS;
     for (int rr = lo + tid; rr < nr; rr += PT) {
       const int i = r0 + rr;
       if (i > j) {
-        if (has) tj[rr] = tauj == T(0) ? T(0) : tj[rr] / d;
+        if (has) tj[rr] = tauj == T(0) ? T(0) : tj[rr] * rd;
       } else if (has) {
         tj[rr] = beta;
       }
