@@ -294,50 +294,12 @@ __global__ void __launch_bounds__(PT) k_qrcp_apply(int j, int nsteps, PanelArgs 
 
 // ------------------------------------------------------------ T factor
 // T(0:j, j) = -tau_j T(0:j, 0:j) (V^T V)(0:j, j), T(j, j) = tau_j (Sec. 5.1),
-// one CTA. When kb^2 values fit in shared memory (kb <= 160 in FP64) the
-// strict upper triangle of the Gram matrix and the upper triangle of T are
-// kept there packed by columns (column l of T at l(l+1)/2, column j of the
-// Gram matrix at j(j-1)/2), so a step reads no global memory; two threads
-// share each row's dot product. Otherwise T is built in global memory.
+// column by column in one CTA, T built in global memory. Used only when the
+// Gram triangle of k_larft_inv below does not fit in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_larft_tri(int kb, const T* __restrict__ gram, int ldg, const T* tau, T* Tm,
-                                                   int ldt, int use_smem) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                   int ldt) {
   const int tid = threadIdx.x;
-  if (use_smem) {
-    T* Tp = reinterpret_cast<T*>(smem_raw);     // kb (kb + 1) / 2
-    T* Gp = Tp + (size_t)kb * (kb + 1) / 2;     // kb (kb - 1) / 2
-    for (int j = 1; j < kb; ++j)
-      for (int l = tid; l < j; l += blockDim.x) Gp[(size_t)j * (j - 1) / 2 + l] = gram[l + (size_t)j * ldg];
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-      const T tj = tau[j];
-      const T* gj = Gp + (size_t)j * (j - 1) / 2;
-      T* tjcol = Tp + (size_t)j * (j + 1) / 2;
-      for (int base = 0; base < j; base += (int)blockDim.x / 2) {
-        const int i = base + (tid >> 1), h = tid & 1;
-        T s0 = T(0), s1 = T(0);
-        if (i < j) {
-          int l = i + h;
-          for (; l + 2 < j; l += 4) {
-            s0 += Tp[(size_t)l * (l + 1) / 2 + i] * gj[l];
-            s1 += Tp[(size_t)(l + 2) * (l + 3) / 2 + i] * gj[l + 2];
-          }
-          if (l < j) s0 += Tp[(size_t)l * (l + 1) / 2 + i] * gj[l];
-        }
-        T s = s0 + s1;
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        if (i < j && h == 0) tjcol[i] = -tj * s;
-      }
-      if (tid == 0) tjcol[j] = tj;
-      __syncthreads();
-    }
-    for (int e = tid; e < kb * kb; e += blockDim.x) {
-      const int i = e % kb, c = e / kb;
-      Tm[i + (size_t)c * ldt] = i <= c ? Tp[(size_t)c * (c + 1) / 2 + i] : T(0);
-    }
-    return;
-  }
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int i = e % kb, c = e / kb;
     Tm[i + (size_t)c * ldt] = T(0);
@@ -588,11 +550,7 @@ void larft_tri(const Ctx& c, int kb, const T* gram, int ldg, const T* tau, T* Tm
     note_launch(c);
     return;
   }
-  const size_t need = sizeof(T) * (size_t)kb * kb;
-  const int use_smem = need <= 200 * 1024 ? 1 : 0;
-  const size_t sm = use_smem ? need : 0;
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_larft_tri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_larft_tri<T><<<1, 256, sm, c.stream>>>(kb, gram, ldg, tau, Tm, ldt, use_smem);
+  k_larft_tri<T><<<1, 256, 0, c.stream>>>(kb, gram, ldg, tau, Tm, ldt);
   note_launch(c);
 }
 

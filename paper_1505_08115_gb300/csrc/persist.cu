@@ -328,11 +328,8 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
 }
 
 // ------------------------------------------------------------ panel
-// Householder QR of an mp x nc panel (Sec. 3.2) as one cooperative launch:
-// each CTA keeps its rows of all nc columns in shared memory for the whole
-// panel; per column the same fused update / next-column partial sums as the
-// multi-launch k_panel_step (panel.cu), separated by the grid barrier, whose
-// last arriver prepares the next column's coefficients.
+// Arguments of the persistent panel QR below: the panel, its tau, and the
+// exchange buffers (per-CTA partial sums, the published row j+1, the totals).
 template <typename T>
 struct QArgs {
   int mp, nc, R;
