@@ -177,6 +177,34 @@ def test_larft_equals_product_of_reflectors(m, k):
     np.testing.assert_allclose(oracle.apply_block(V, T, C, trans=False), prod @ C, atol=1e-13)
 
 
+@pytest.mark.parametrize("m,k,zero", [(30, 8, None), (100, 17, None), (40, 12, 5), (64, 64, 0)])
+def test_larft_inverse_is_tau_plus_strict_gram(m, k, zero):
+    """S = diag(1/tau) + striu(V^T V) grows by the same column recursion as T
+    (Sec. 5.1 remark), so T S = I. With tau_i = 0 (no reflector) row and column
+    i of T vanish, and the back substitution x_j = tau_j,
+    x_i = -tau_i sum_{k=i+1..j} G_ik x_k still gives column j of T."""
+    r = np.random.default_rng(m + k)
+    V = np.tril(r.standard_normal((m, k)), -1) + np.eye(m, k)
+    tau = 2.0 / np.sum(V * V, axis=0)  # reflectors I - tau v v^T orthogonal
+    if zero is not None:
+        tau[zero] = 0.0
+    T = oracle.larft(V, tau)
+    G = V.T @ V
+    Tb = np.zeros((k, k))
+    for j in range(k):
+        x = np.zeros(k)
+        x[j] = tau[j]
+        for i in range(j - 1, -1, -1):
+            x[i] = -tau[i] * (G[i, i + 1:j + 1] @ x[i + 1:j + 1])
+        Tb[:, j] = x
+    np.testing.assert_allclose(T, Tb, rtol=0, atol=1e-13 * max(1.0, np.abs(T).max()))
+    if zero is None:
+        S = np.diag(1.0 / tau) + np.triu(G, 1)
+        np.testing.assert_allclose(T @ S, np.eye(k), rtol=0, atol=1e-12)
+    else:
+        assert np.all(T[zero, :] == 0) and np.all(T[:, zero] == 0)
+
+
 # --------------------------------------------- Sec. 4.1/4.3/5.1/5.2 (rqrcp)
 def _check_factorization(A, F, T, perm, b, tol=1e-13):
     m, n = A.shape
