@@ -20,7 +20,8 @@
 //    window of 128 K is below (a + 1) 128 127^2 2^(-7a) < 2^(24 - 7a), so every
 //    slot holds an exact integer S_a 2^(-7a) in FP32.
 // 3. Drain (epilogue warps), once per window of 128 K: slots 0..5 are
-//    converted to integers and added into H = sum_{a<=5} S_a 2^(7(5-a))
+//    converted to integers, paired in 32 bits (S_2k 2^7 + S_2k+1 < 2^31) and
+//    added into H = sum_{a<=5} S_a 2^(7(5-a))
 //    (int64; below 2^57 per window, at most 64 windows per tile), slots 6 and 7
 //    (weights 2^-42 and below relative to the leading term) into a float M6,
 //    whose rounding stays below 2^-58 of the product's scale. At the end of
