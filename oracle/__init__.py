@@ -67,6 +67,7 @@ def lib():
             L.orc_rurv_diag.restype = c_int
             L.orc_jacobi_svd.argtypes = [c_int, c_int, d, c_int, d, d, c_int]
             L.orc_jacobi_svd.restype = c_int
+            L.orc_complete_column.argtypes = [c_int, c_int, d, c_int]
             u32p = ctypes.POINTER(ctypes.c_uint32)
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.orc_gauss_fill.argtypes = [c_u64, c_u64, c_i64, d]
@@ -213,6 +214,14 @@ def jacobi_svd(M):
     J = np.zeros((c, c), order="F")
     lib().orc_jacobi_svd(r, c, _dp(M), r, _dp(sv), _dp(J), c)
     return M, sv, J
+
+
+def complete_column(V, c):
+    """Sec. 6.2: V with column c set orthonormal to its columns 0..c-1."""
+    V = _f64(V)
+    bi = V.shape[0]
+    lib().orc_complete_column(bi, c, _dp(V), bi)
+    return V
 
 
 def philox4x32_10(ctr, key):

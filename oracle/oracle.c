@@ -446,14 +446,48 @@ static int thin_qr(int r, int c, const double* Z, int ldz, double* Q, int ldq, d
   return kq;
 }
 
+/* ------------------------------------------------ Sec. 6.2 completion */
+/* Column c of the bi x bi matrix V (ld ldv), orthogonal to its orthonormal
+ * columns 0..c-1, for a zero singular value: the first unit vector e_k that
+ * Gram-Schmidt (twice) against those columns leaves with norm above 1/2, or,
+ * if none does, the one left with the largest norm (at least (bi-c)/bi in
+ * squared norm, summed over k), normalised. */
+void orc_complete_column(int bi, int c, double* V, int ldv) {
+  double* v = V + IX(0, c, ldv);
+  int best = 0;
+  double best_nv = -1.0;
+  for (int pick = 0; pick < 2; ++pick) {
+    for (int e = 0; e < bi; ++e) {
+      if (pick == 1 && e != best) continue;
+      for (int i = 0; i < bi; ++i) v[i] = (i == e) ? 1.0 : 0.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < c; ++t) {
+          const double* u = V + IX(0, t, ldv);
+          double d = 0.0;
+          for (int i = 0; i < bi; ++i) d += u[i] * v[i];
+          for (int i = 0; i < bi; ++i) v[i] -= d * u[i];
+        }
+      double nv = 0.0;
+      for (int i = 0; i < bi; ++i) nv += v[i] * v[i];
+      nv = sqrt(nv);
+      if (nv > 0.5 || pick == 1) {
+        for (int i = 0; i < bi; ++i) v[i] /= nv;
+        return;
+      }
+      if (nv > best_nv) {
+        best_nv = nv;
+        best = e;
+      }
+    }
+  }
+}
+
 /* ------------------------------------------------ Sec. 4.2, 6.3, 6.4 */
 /* Sec. 6.2 (Fig. blockRRQR): diagonalise the bi x bi diagonal block R11 of the
  * block that starts at k0, after its left QR and trailing update. The SVD is
  * R11 = U' D Vt^T: one-sided Jacobi on M = R11^T gives M J = Vt D with J = U'
  * (columns sorted by descending norm); the columns of Vt are those of M J over
- * their norms, and a zero column is replaced by the first unit vector that
- * Gram-Schmidt (twice) against the columns already set leaves with norm above
- * 1/2. Then A(0:k0, block) <- A(0:k0, block) Vt, R12 <- U'^T R12, R11 <- D
+ * their norms, and a zero column is completed by orc_complete_column. Then A(0:k0, block) <- A(0:k0, block) Vt, R12 <- U'^T R12, R11 <- D
  * (the strictly lower part of the block, the Householder vectors, is kept),
  * and U' and Vt go to DU(0:bi, k0:k0+bi) and DV(0:bi, k0:k0+bi). */
 static void diag_block(int n, double* A, int lda, int k0, int bi, double* DU, int lddu, double* DV, int lddv) {
@@ -472,24 +506,7 @@ static void diag_block(int n, double* A, int lda, int k0, int bi, double* DU, in
       for (int i = 0; i < bi; ++i) Vt[IX(i, c, lddv)] = M[IX(i, c, bi)] / sv[c];
       continue;
     }
-    for (int e = 0; e < bi; ++e) {
-      double* v = Vt + IX(0, c, lddv);
-      for (int i = 0; i < bi; ++i) v[i] = (i == e) ? 1.0 : 0.0;
-      for (int pass = 0; pass < 2; ++pass)
-        for (int t = 0; t < c; ++t) {
-          const double* u = Vt + IX(0, t, lddv);
-          double d = 0.0;
-          for (int i = 0; i < bi; ++i) d += u[i] * v[i];
-          for (int i = 0; i < bi; ++i) v[i] -= d * u[i];
-        }
-      double nv = 0.0;
-      for (int i = 0; i < bi; ++i) nv += v[i] * v[i];
-      nv = sqrt(nv);
-      if (nv > 0.5) {
-        for (int i = 0; i < bi; ++i) v[i] /= nv;
-        break;
-      }
-    }
+    orc_complete_column(bi, c, Vt, lddv);
   }
   /* A(0:k0, block) <- A(0:k0, block) Vt */
   double* row = (double*)xcalloc((size_t)bi, sizeof(double));

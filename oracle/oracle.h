@@ -110,6 +110,10 @@ int orc_rurv_diag(int m, int n, double* A, int lda, int b, int p, int q, int k, 
  * M*J): on exit sv[c] holds the column norms of M*J sorted descending and J
  * (c x c, ldj) the matching right singular vectors. Returns the sweep count. */
 int orc_jacobi_svd(int r, int c, double* M, int ldm, double* sv, double* J, int ldj);
+/* Sec. 6.2: column c of V (bi x bi, ld ldv) for a zero singular value, from
+ * the orthonormal columns 0..c-1 (the first unit vector Gram-Schmidt leaves
+ * with norm above 1/2, else the one left with the largest norm). */
+void orc_complete_column(int bi, int c, double* V, int ldv);
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): one block. */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -179,7 +179,8 @@ void jacobi_svd(const Ctx& c, int r, int cols, double* M, int ldm, double* J, in
 // M = R11^T J from jacobi_svd (unsorted columns), `order` and the sorted norms
 // sv, the right factor Vt(:, c) = M(:, order[c]) / sv[c]; a zero norm gets the
 // first unit vector that two Gram-Schmidt passes against the columns already set
-// leave with norm above 1/2. U' = Js is copied to DU, Vt to DV, and the upper
+// leave with norm above 1/2, or, if none does, the one they leave with the
+// largest norm, normalised. U' = Js is copied to DU, Vt to DV, and the upper
 // triangle of the block (F, ld ldf) becomes diag(sv). One CTA.
 __global__ void __launch_bounds__(256) k_diag_finish(int bi, const double* __restrict__ M, int ldm,
                                                      const int* __restrict__ order, const double* __restrict__ sv,
@@ -201,7 +202,9 @@ __global__ void __launch_bounds__(256) k_diag_finish(int bi, const double* __res
       __syncthreads();
       continue;
     }
-    for (int e = 0; e < bi; ++e) {
+    // unit vector e_k, Gram-Schmidt twice against columns 0..c-1; returns the
+    // residual norm (the same value in every thread)
+    auto project_unit = [&](int e) -> double {
       for (int i = tid; i < bi; i += blockDim.x) v[i] = (i == e) ? 1.0 : 0.0;
       __syncthreads();
       for (int pass = 0; pass < 2; ++pass)
@@ -233,13 +236,25 @@ __global__ void __launch_bounds__(256) k_diag_finish(int bi, const double* __res
         s_norm = sqrt(sum);
       }
       __syncthreads();
-      nv = s_norm;
+      return s_norm;
+    };
+    // the first e_k left with norm above 1/2, else the one left with the
+    // largest norm (their squared norms add up to bi - c >= 1)
+    int best = 0;
+    double best_nv = -1.0, nv = -1.0;
+    bool done = false;
+    for (int e = 0; e < bi && !done; ++e) {
+      nv = project_unit(e);
       if (nv > 0.5) {
-        for (int i = tid; i < bi; i += blockDim.x) v[i] /= nv;
-        __syncthreads();
-        break;
+        done = true;
+      } else if (nv > best_nv) {
+        best_nv = nv;
+        best = e;
       }
     }
+    if (!done) nv = project_unit(best);
+    for (int i = tid; i < bi; i += blockDim.x) v[i] /= nv;
+    __syncthreads();
   }
   for (int e = tid; e < bi * bi; e += blockDim.x) {
     const int i = e % bi, j = e / bi;

@@ -408,6 +408,27 @@ def test_rurv_diag_rank_deficient_completes_vt():
     assert abs(R[0, 0] - np.sqrt(m)) <= 1e-12 and np.linalg.norm(R) == pytest.approx(np.sqrt(m), rel=1e-13)
 
 
+@pytest.mark.parametrize("bi", [8, 32])
+def test_diag_completion_when_no_unit_vector_is_half_outside(bi):
+    """Completion of Vt for a zero singular value (Sec. 6.2) when the span of
+    the set columns leaves every unit vector with residual norm 1/sqrt(bi) < 1/2:
+    the largest residual is taken, so the column is the unit normal w."""
+    w = np.ones(bi) / np.sqrt(bi)
+    X = np.random.default_rng(bi).standard_normal((bi, bi))
+    X[:, 0] = w
+    Q, _ = np.linalg.qr(X)
+    V = np.zeros((bi, bi), order="F")
+    V[:, :bi - 1] = Q[:, 1:]
+    V = oracle.complete_column(V, bi - 1)
+    np.testing.assert_allclose(V.T @ V, np.eye(bi), atol=1e-14)
+    assert abs(abs(V[:, -1] @ w) - 1.0) <= 1e-14
+    # and the usual case: a unit vector with residual above 1/2 is taken as is
+    V2 = np.zeros((bi, bi), order="F")
+    V2[:, 0] = Q[:, 0]
+    V2 = oracle.complete_column(V2, 1)
+    np.testing.assert_allclose(V2[:, :2].T @ V2[:, :2], np.eye(2), atol=1e-14)
+
+
 def test_rurv_gap_gives_block_diagonal():
     # A = U diag(s) V^T with a 1e8 gap at a block boundary; with q = 2, p = b the
     # first block's S captures the top right singular space, so R12 is tiny.
