@@ -22,8 +22,9 @@ SO_PATH = os.path.join(_HERE, "librqr.so")
 
 FP64, FP32, FP64X = 0, 1, 2
 SKETCH_DOWNDATE, SKETCH_RESAMPLE = 0, 1
-STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 4: "workspace too small",
-          5: "unsupported combination", 6: "invalid handle", 7: "problem larger than the fixed internal buffer"}
+STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 3: "a bounded wait in a kernel ran out",
+          4: "workspace too small", 5: "unsupported combination", 6: "invalid handle",
+          7: "problem larger than the fixed internal buffer"}
 FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 
 # every symbol declared in include/rqr.h

@@ -54,3 +54,63 @@ def test_argument_validation_without_gpu(lib):
     assert sz.value > 100 * 80
     lib.rqr_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.rqr_version()
+
+
+def _ws(L, m, n, b, p, q=-1, prec=0, sketch=0):
+    sz = ctypes.c_size_t()
+    rc = L.rqr_workspace_bytes(m, n, b, p, q, prec, sketch, ctypes.byref(sz))
+    return rc, sz.value
+
+
+def test_workspace_bytes_argument_codes():
+    from paper_1505_08115_gb300 import rqr
+    L = rqr.load()
+    # (m, n, b, p, q, prec, sketch) -> the 1-based index of the rejected argument
+    bad = [((-1, 0, 8, 2, -1, 0, 0), 1), ((10, 11, 8, 2, -1, 0, 0), 2), ((10, -1, 8, 2, -1, 0, 0), 2),
+           ((10, 10, 0, 2, -1, 0, 0), 3), ((10, 10, 513, 2, -1, 0, 0), 3), ((10, 10, 8, -1, -1, 0, 0), 4),
+           ((10, 10, 8, 2, -1, 7, 0), 6), ((10, 10, 8, 2, -1, 0, 5), 7),
+           ((10, 10, 8, 2, 1, 1, 0), 6), ((10, 10, 8, 2, 1, 2, 0), 6)]  # the URV method is FP64 only
+    for args, pos in bad:
+        assert _ws(L, *args)[0] == -pos, args
+    assert L.rqr_workspace_bytes(10, 10, 8, 2, -1, 0, 0, None) == -8
+    assert _ws(L, 0, 0, 8, 2) == (0, _ws(L, 0, 0, 8, 2)[1])
+
+
+def test_workspace_bytes_sizes():
+    """The sizes the data layout states: at n = 16384, b = 128, p = 8 about
+    0.2 GB in FP64 and 1.3 GB with the FP64X digit planes; FP32 half of FP64;
+    the resampled sketch needs no more than the downdated one."""
+    from paper_1505_08115_gb300 import rqr
+    L = rqr.load()
+    rc, w64 = _ws(L, 16384, 16384, 128, 8, prec=0)
+    assert rc == 0 and 0.15e9 < w64 < 0.25e9
+    rc, w64x = _ws(L, 16384, 16384, 128, 8, prec=2)
+    assert rc == 0 and 1.2e9 < w64x < 1.4e9
+    rc, w32 = _ws(L, 16384, 16384, 128, 8, prec=1)
+    assert rc == 0 and abs(w32 - w64 / 2) <= 0.01 * w64
+    assert _ws(L, 16384, 16384, 128, 8, sketch=1)[1] <= w64
+    sizes = [_ws(L, n, n, 128, 8)[1] for n in (256, 1000, 4096, 8192, 16384)]
+    assert sizes == sorted(sizes)
+    assert _ws(L, 8192, 8192, 128, 10, q=2)[0] == 0
+
+
+def test_null_handle_is_argument_one_everywhere():
+    """Every call that takes a handle rejects NULL before touching the device;
+    rqr_create answers a missing device with RQR_ERR_CUDA and a NULL handle."""
+    from paper_1505_08115_gb300 import rqr
+    import torch
+    L = rqr.load()
+    z = ctypes.c_size_t(0)
+    assert L.rurv_factor(None, 10, 10, None, 10, 4, 2, 1, 0, 1, None, None, 4, None, 10, None, 4, None, 4, None, 4,
+                         0, None, z, None) == -1
+    assert L.rqr_form_q(None, 10, 10, 4, None, 10, None, 4, None, 10, 10, 0, None, z) == -1
+    assert L.rqr_form_q_noalloc(None, 10, 10, 4, None, 10, None, 4, None, 10, 10, 0) == -1
+    assert L.rqr_gemm(None, 0, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, z) == -1
+    assert L.rqr_gauss_fill(None, 1, 0, 4, None, 0) == -1
+    assert L.rqr_philox_raw(None, 0, 0, 0, 0, 0, 4, None) == -1
+    assert L.rqr_profile_enable(None, 1) == -1
+    assert L.rqr_destroy(None) == 6 and L.rqr_set_stream(None, None) == 6   # RQR_ERR_HANDLE
+    assert L.rqr_create(None, None) == -1
+    if not torch.cuda.is_available():
+        h = ctypes.c_void_p(1)
+        assert L.rqr_create(ctypes.byref(h), None) == 1 and not h.value   # RQR_ERR_CUDA
