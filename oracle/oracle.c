@@ -21,6 +21,26 @@
  *  - p is the over-sampling parameter (Sec. 4.3 calls it r); l = b + p.
  *  - URV: orthonormalisation between power steps (Sec. 6.3 prints the power
  *    without it) and the l -> b reduction through the SVD of the sketch's R.
+ *  - Sec. 6.2 completion of Vt for a zero singular value: the first unit
+ *    vector left with norm above 1/2 by Gram-Schmidt, else the largest.
+ *
+ * What pins each routine (tests/test_oracle_pins.py, CPU), other than itself:
+ *  orc_house         the worked examples of Sec. 3.1, the unit-vector form of H
+ *  orc_qrcp          closed-form pivots of orthogonal columns, brute-force
+ *                    greedy selection on tiny inputs, LAPACK dgeqp3 (scipy)
+ *  orc_geqr2         LAPACK dgeqrf (scipy)
+ *  orc_larft         the product of the reflectors; T^-1 = diag(1/tau) +
+ *                    striu(V^T V) and its back substitution
+ *  orc_apply_block   the product of the reflectors
+ *  orc_rqrcp(_ex)    G = I reduces it to Fig. QR; the sketch stays G X''; gap-
+ *                    separated pivot sets; ||R||_F = ||A||_F, sum log|R_ii|
+ *  orc_rurv(_diag)   Eckart-Young lower bounds, the gap case, diagonal blocks
+ *                    equal to the SVDs (LAPACK) of the undiagonalised blocks
+ *  orc_jacobi_svd    LAPACK SVD (numpy)
+ *  orc_complete_column  orthonormality, and the all-ones complement case
+ *  orc_philox4x32_10 the published known-answer vectors
+ *  orc_gauss_fill    moments of N(0, 1) and prefix consistency of the stream
+ * Parity unpinned (statistical only): the paper's qualitative Sec. 7 claims.
  */
 #include "oracle.h"
 #include <math.h>
