@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -81,7 +82,9 @@ class Clocks:
     def __init__(self, device_index: str):
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: a temporary file, or RQR_BENCH_CLOCKS_DIR when the caller wants to keep them
+        d = os.environ.get("RQR_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
