@@ -75,7 +75,8 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
  *   m, n     rows and columns, m >= n >= 0.
  *   A        (device, in/out) m x n, ld lda. On exit R is in the upper triangle
  *            and the Householder vectors of every block below the diagonal.
- *   b        block size, 1 <= b; p >= 0 over-sampling; the sketch has l = b + p rows.
+ *   b        block size, 1 <= b <= 512; p >= 0 over-sampling, b + p <= 1024; the
+ *            sketch has l = b + p rows.
  *   seed     Philox4x32-10 key for the Gaussian sketch when G == NULL.
  *   G        (device, optional) the Gaussian: DOWNDATE: l x m, ld ldg.
  *            RESAMPLE: the blocks G_i (l x (m - k0)), ld l, one after another,
@@ -98,7 +99,8 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
  * 6.3, 6.4; Method 2 of Sec. 7, and with the power scheme and DU, DV given,
  * Method 3 / Fig. blockRRQR with diagonalised diagonal blocks, Sec. 6.2).
  *   A        (device, in/out) m x n, ld lda: R above, left reflectors below.
- *   b, p, q  block size, over-sampling (l = b + p), power steps q >= 0.
+ *   b, p, q  block size 1 <= b <= 512, over-sampling p >= 0 (l = b + p <= 1024),
+ *            power steps 0 <= q <= 64.
  *   k        stop once k0 >= k (truncated rank-k URV); k <= 0 or k >= n: full.
  *   seed, G  Gaussian blocks G_i (l x (m - k0), ld l, one after another,
  *            one per block including the last), or NULL to draw from seed.
@@ -112,6 +114,8 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
  *            <- A(0:k0, block) Vt, R12 <- U'^T R12, R11 <- D (descending); U' is
  *            stored at DU(0:b_i, k0:k0+b_i), Vt at DV(0:b_i, k0:k0+b_i). Then
  *            Q = Q_house blockdiag(U'_i) and P = S_0 S_1 ... blockdiag(Vt_i).
+ *            A zero singular value gets the column of Vt that completes the
+ *            others to an orthonormal basis (Gram-Schmidt of a unit vector).
  *   prec     RQR_FP64. */
 int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k,
                 uint64_t seed, const void* G, void* TU, int ldtu, void* WV, int ldwv, void* TV,
