@@ -114,3 +114,23 @@ def test_null_handle_is_argument_one_everywhere():
     if not torch.cuda.is_available():
         h = ctypes.c_void_p(1)
         assert L.rqr_create(ctypes.byref(h), None) == 1 and not h.value   # RQR_ERR_CUDA
+
+
+def test_product_path_fails_loudly_without_the_library_or_a_gpu():
+    """No CPU fallback: a missing library and host tensors raise instead of computing."""
+    import subprocess
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1505_08115_gb300 import rqr\n"
+            "try:\n    rqr.load('/nonexistent/librqr.so')\nexcept RuntimeError as e:\n    print('raised', e)\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.startswith("raised"), out.stdout + out.stderr
+    import torch
+
+    from paper_1505_08115_gb300 import rqr
+
+    with pytest.raises(RuntimeError):
+        rqr.rqrcp_factor(torch.zeros(8, 8, dtype=torch.float64), 4, 2)
+    with pytest.raises(RuntimeError):
+        rqr.gemm(torch.zeros(4, 4, dtype=torch.float64), torch.zeros(4, 4, dtype=torch.float64))
