@@ -68,6 +68,7 @@ def lib():
             L.orc_jacobi_svd.argtypes = [c_int, c_int, d, c_int, d, d, c_int]
             L.orc_jacobi_svd.restype = c_int
             L.orc_complete_column.argtypes = [c_int, c_int, d, c_int]
+            L.orc_reduce_sketch.argtypes = [c_int, c_int, c_int, d, c_int, d, c_int]
             u32p = ctypes.POINTER(ctypes.c_uint32)
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.orc_gauss_fill.argtypes = [c_u64, c_u64, c_i64, d]
@@ -214,6 +215,16 @@ def jacobi_svd(M):
     J = np.zeros((c, c), order="F")
     lib().orc_jacobi_svd(r, c, _dp(M), r, _dp(sv), _dp(J), c)
     return M, sv, J
+
+
+def reduce_sketch(Z, b):
+    """The l -> b reduction of the orthonormal pivot: an r x b orthonormal
+    basis of the b dominant left singular vectors of the r x c sketch Z."""
+    Z = _f64(Z)
+    r, c = Z.shape
+    Zr = np.zeros((r, b), order="F")
+    lib().orc_reduce_sketch(r, c, b, _dp(Z), r, _dp(Zr), r)
+    return Zr
 
 
 def complete_column(V, c):

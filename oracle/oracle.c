@@ -36,6 +36,9 @@
  *                    separated pivot sets; ||R||_F = ||A||_F, sum log|R_ii|
  *  orc_rurv(_diag)   Eckart-Young lower bounds, the gap case, diagonal blocks
  *                    equal to the SVDs (LAPACK) of the undiagonalised blocks
+ *  orc_reduce_sketch the projector onto the b dominant left singular
+ *                    vectors of Z (numpy SVD), on inputs where it differs
+ *                    by O(1) from the span of Z's first b columns
  *  orc_jacobi_svd    LAPACK SVD (numpy)
  *  orc_complete_column  orthonormality, and the all-ones complement case
  *  orc_philox4x32_10 the published known-answer vectors
@@ -466,6 +469,28 @@ static int thin_qr(int r, int c, const double* Z, int ldz, double* Q, int ldq, d
   return kq;
 }
 
+/* ------------------------------------------------ Sec. 4.2 + 4.3 reduction */
+void orc_reduce_sketch(int r, int c, int b, const double* Z, int ldz, double* Zr, int ldzr) {
+  int kk = r < c ? r : c;
+  double* Qz = (double*)xcalloc((size_t)r * kk, sizeof(double));
+  double* Rz = (double*)xcalloc((size_t)kk * c, sizeof(double));
+  thin_qr(r, c, Z, ldz, Qz, r, Rz, kk);
+  /* one-sided Jacobi on M = Rz^T (c x kk): J = left singular vectors of Rz */
+  double* M = (double*)xcalloc((size_t)c * kk, sizeof(double));
+  for (int j = 0; j < kk; ++j)
+    for (int i = 0; i < c; ++i) M[IX(i, j, c)] = Rz[IX(j, i, kk)];
+  double* sv = (double*)xcalloc((size_t)kk, sizeof(double));
+  double* J = (double*)xcalloc((size_t)kk * kk, sizeof(double));
+  orc_jacobi_svd(c, kk, M, c, sv, J, kk);
+  /* Zr = Qz J(:, 0:b): the b dominant left singular vectors of Z */
+  matmul_nn(r, b, kk, Qz, r, J, kk, Zr, ldzr);
+  free(Qz);
+  free(Rz);
+  free(M);
+  free(sv);
+  free(J);
+}
+
 /* ------------------------------------------------ Sec. 6.2 completion */
 /* Column c of the bi x bi matrix V (ld ldv), orthogonal to its orthonormal
  * columns 0..c-1, for a zero singular value: the first unit vector e_k that
@@ -602,25 +627,9 @@ int orc_rurv_diag(int m, int n, double* A, int lda, int b, int p, int q, int k, 
     double* Zb = Z;
     double* Zr = NULL;
     if (zc > bi) {
-      int kk = np < zc ? np : zc;
-      double* Qz = (double*)xcalloc((size_t)np * kk, sizeof(double));
-      double* Rz = (double*)xcalloc((size_t)kk * zc, sizeof(double));
-      thin_qr(np, zc, Z, np, Qz, np, Rz, kk);
-      /* one-sided Jacobi on M = Rz^T (zc x kk): J = left singular vectors of Rz */
-      double* M = (double*)xcalloc((size_t)zc * kk, sizeof(double));
-      for (int j = 0; j < kk; ++j)
-        for (int i = 0; i < zc; ++i) M[IX(i, j, zc)] = Rz[IX(j, i, kk)];
-      double* sv = (double*)xcalloc((size_t)kk, sizeof(double));
-      double* J = (double*)xcalloc((size_t)kk * kk, sizeof(double));
-      orc_jacobi_svd(zc, kk, M, zc, sv, J, kk);
       Zr = (double*)xcalloc((size_t)np * bi, sizeof(double));
-      matmul_nn(np, bi, kk, Qz, np, J, kk, Zr, np);
+      orc_reduce_sketch(np, zc, bi, Z, np, Zr, np);
       Zb = Zr;
-      free(Qz);
-      free(Rz);
-      free(M);
-      free(sv);
-      free(J);
     }
     /* Householder QR of Z (n' x b_i) gives S = I - W TS W^T (Sec. 4.2) */
     double* taus = (double*)xcalloc((size_t)bi, sizeof(double));

@@ -106,6 +106,15 @@ int orc_rurv_diag(int m, int n, double* A, int lda, int b, int p, int q, int k, 
                   double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, double* DU, int lddu,
                   double* DV, int lddv);
 
+/* The l -> b reduction of the orthonormal pivot (Sec. 4.2 with the
+ * over-sampling of Sec. 4.3), the step orc_rurv applies to its r x c sketch
+ * Z when c > b: thin Householder QR Z = Qz Rz, one-sided Jacobi SVD of
+ * Rz^T (whose right singular vectors are the left ones of Rz, sorted by
+ * descending singular value), Zr (r x b, ld ldzr) = Qz Ur(:, 0:b). So Zr is an
+ * orthonormal basis of the b dominant left singular vectors of Z (b <= min(r, c)).
+ * Pinned against the projector of numpy's SVD of Z. */
+void orc_reduce_sketch(int r, int c, int b, const double* Z, int ldz, double* Zr, int ldzr);
+
 /* One-sided Jacobi SVD (Hestenes 1958) of the r x c matrix M (overwritten by
  * M*J): on exit sv[c] holds the column norms of M*J sorted descending and J
  * (c x c, ldj) the matching right singular vectors. Returns the sweep count. */

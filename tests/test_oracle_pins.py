@@ -478,6 +478,70 @@ def test_methods_quality_order_statistical():
     assert wins >= 0.8 * 3 * len(range(b, n, b))
 
 
+def _projector(B):
+    return B @ B.T
+
+
+@pytest.mark.parametrize("r,c,b,seed", [(60, 14, 8, 1), (200, 40, 32, 2), (35, 35, 20, 3), (128, 138, 128, 4)])
+def test_reduce_sketch_spans_dominant_singular_subspace(r, c, b, seed):
+    """The l -> b reduction (Sec. 4.2, 4.3) returns an orthonormal basis of the
+    b dominant left singular vectors of Z: its projector equals U_b U_b^T from
+    LAPACK's SVD (through numpy). Z has a clear gap after sigma_b (a factor 10)
+    so that the subspace is well determined."""
+    g = np.random.default_rng(seed)
+    k = min(r, c)
+    U, _ = np.linalg.qr(g.standard_normal((r, k)))
+    V, _ = np.linalg.qr(g.standard_normal((c, k)))
+    s = np.concatenate([np.linspace(10.0, 5.0, b), np.linspace(0.5, 0.01, k - b)])
+    Z = (U * s) @ V.T
+    Zr = oracle.reduce_sketch(Z, b)
+    assert Zr.shape == (r, b)
+    np.testing.assert_allclose(Zr.T @ Zr, np.eye(b), atol=1e-13)
+    Us = np.linalg.svd(Z, full_matrices=False)[0][:, :b]
+    assert np.abs(_projector(Zr) - _projector(Us)).max() <= 1e-12
+
+
+def test_reduce_sketch_is_not_the_leading_columns():
+    """A case that separates the reduction from keeping the first b columns of
+    the orthonormal factor of Z (the paper-literal "first b steps" of an
+    unpivoted QR): the first b columns of Z are tiny, the dominant subspace
+    lies in the span of the other columns. The result must follow the SVD, and
+    the leading-columns reading must miss it by O(1)."""
+    g = np.random.default_rng(9)
+    r, b, p = 50, 4, 8
+    Z = g.standard_normal((r, b + p))
+    Z[:, :b] *= 1e-6
+    Zr = oracle.reduce_sketch(Z, b)
+    Us = np.linalg.svd(Z, full_matrices=False)[0][:, :b]
+    assert np.abs(_projector(Zr) - _projector(Us)).max() <= 1e-10
+    Qz = np.linalg.qr(Z)[0][:, :b]
+    assert np.abs(_projector(Qz) - _projector(Us)).max() >= 0.1
+    # a reversed order (the b smallest singular directions) would fail too
+    Ul = np.linalg.svd(Z, full_matrices=False)[0][:, -b:]
+    assert np.abs(_projector(Zr) - _projector(Ul)).max() >= 0.1
+
+
+def test_rurv_uses_the_reduction():
+    """orc_rurv's first block takes its orthonormal pivot from the reduced
+    sketch: with q = 0 the first Householder vectors of S_0 (stored in WV)
+    reproduce the reduction of Z = (G_0 A)^T, up to the column signs of the
+    Householder basis."""
+    g = np.random.default_rng(11)
+    m, n, b, p = 80, 60, 8, 6
+    A = np.asfortranarray(g.standard_normal((m, n)))
+    G = inputs.resample_blocks(12, m, n, b, p)
+    l = b + p
+    G0 = G[: l * m].reshape((l, m), order="F")
+    Zr = oracle.reduce_sketch((G0 @ A).T, b)
+    F, TU, WV, TV, done = oracle.rurv(A, b, p, 0, G, k=b)
+    assert done == b
+    W = np.tril(WV[:, :b], -1)
+    W[np.arange(b), np.arange(b)] = 1.0
+    S = np.eye(n) - W @ TV[:b, :b] @ W.T
+    # the first b columns of S span the same subspace as Zr
+    assert np.abs(_projector(S[:, :b]) - _projector(Zr)).max() <= 1e-12
+
+
 # --------------------------------------------------------- one-sided Jacobi
 @pytest.mark.parametrize("r,c", [(10, 10), (30, 12), (40, 40)])
 def test_jacobi_svd_against_lapack(r, c):
