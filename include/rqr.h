@@ -46,9 +46,12 @@ typedef struct rqr_handle_s* rqr_handle_t;
 
 /* Runtime status codes (positive return values / *info). */
 #define RQR_OK 0
-#define RQR_ERR_CUDA 1        /* a CUDA call failed; the handle stays usable   */
+#define RQR_ERR_CUDA 1        /* a CUDA call failed, or a kernel found an
+                                 internal index out of range and skipped the
+                                 work; the handle stays usable                 */
 #define RQR_ERR_NONFINITE 2   /* a NaN/Inf reached a panel norm               */
-#define RQR_ERR_TIMEOUT 3     /* a bounded wait inside a kernel ran out       */
+#define RQR_ERR_TIMEOUT 3     /* a bounded wait inside a kernel ran out (see
+                                 rqr_set_wait_limit_ns)                         */
 #define RQR_ERR_WORKSPACE 4   /* lwork smaller than rqr_workspace_bytes        */
 #define RQR_ERR_UNSUPPORTED 5 /* a combination this build does not implement  */
 #define RQR_ERR_HANDLE 6      /* NULL or destroyed handle                      */
@@ -64,6 +67,17 @@ int rqr_destroy(rqr_handle_t h);
 
 /* Rebinds the handle to another stream (cudaStream_t). */
 int rqr_set_stream(rqr_handle_t h, void* stream);
+
+/* Limit, in nanoseconds of GPU global time, of every grid-arrival wait of the
+ * cooperative pivot and panel kernels (the steps that exchange values between
+ * all CTAs once per column). A wait that runs out makes the call finish with
+ * RQR_ERR_TIMEOUT in *info: every later kernel of the call sees the status
+ * word and does no swap, panel or pivot work on values of the aborted step
+ * (the output is then undefined, but every access stays inside the caller's
+ * buffers). ns = 0 restores the default of 2 s. The tensor-core product
+ * kernel keeps its own fixed 2 s limit on its pipeline waits. Returns -1 for
+ * an invalid handle. No counterpart in the paper: it bounds device waits. */
+int rqr_set_wait_limit_ns(rqr_handle_t h, uint64_t ns);
 
 /* Bytes of device workspace that rqrcp_factor (q < 0) or rurv_factor (q >= 0)
  * needs for the given shape, block size b, over-sampling p and precision.
@@ -135,13 +149,20 @@ int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, cons
  * output buffers. The paper has no counterpart; it is a deployment aid.
  * Arguments and result are those of rqr_form_q without work/lwork. The
  * scratch is one static device array of RQR_FORM_Q_NOALLOC_MAX_BYTES in the
- * library, present on every GPU that loads it until the process exits; a
- * problem whose scratch (m*b + 2*b*ncols values, plus some for partial sums)
- * does not fit returns RQR_ERR_SIZE and queues nothing. The call allocates
- * nothing. All calls share the array: calls whose GPU work overlaps (other
- * streams or handles on the same device) race on it. The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. */
+ * library, present on every GPU that loads it until the process exits. With
+ * e = 8 (RQR_FP64) or 4 (RQR_FP32) bytes per value and r(x) = x rounded up to
+ * a multiple of 256, a problem is accepted when
+ *   r(m*b*e) + 2 r(b*ncols*e) <= RQR_FORM_Q_NOALLOC_MAX_BYTES
+ * (with m, ncols counted as at least 1), else it returns RQR_ERR_SIZE and
+ * queues nothing; what is left of the array holds split-K partial sums, so
+ * near the limit the products run with fewer K splits or none. The call
+ * allocates nothing. All calls share the array: calls whose GPU work overlaps
+ * (other streams or handles on the same device) race on it. The first call
+ * with a handle of a given device looks up that device's copy of the array
+ * (cudaGetSymbolAddress, with the handle's device made current for the
+ * lookup and the caller's current device restored); make that first call
+ * before any stream capture. The looked-up address does not survive
+ * cudaDeviceReset of that device. */
 #define RQR_FORM_Q_NOALLOC_MAX_BYTES (8u << 20)
 int rqr_form_q_noalloc(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt,
                        void* Q, int ldq, int ncols, int prec);

@@ -52,6 +52,8 @@ struct Ctx {
   int* status;         // device status word (RQR_ERR_* or 0)
   int64_t* nlaunch;    // host-side count of kernel launches (may be null)
   KernelTimer* kt = nullptr;  // optional per-launch timing of the tcgen05 products
+  int device = -1;            // CUDA device of the handle (its stream belongs to it)
+  unsigned long long wait_ns = 2000000000ull;  // limit of the grid-arrival waits of the persistent kernels
 };
 
 // Counts kernel launches issued through a context (tracing aid).
@@ -189,8 +191,10 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
 
 // Applies the swaps (j, picks[j]), j = 0..kb-1, in order to columns k0.. of
 // A (all m rows), to columns y0.. of Y (l rows, optional) and to perm[k0..].
+// np: positions in play (every pick lies in [j, np)); nothing is swapped once
+// the status word is set.
 template <typename T>
-void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy,
+void apply_swaps(const Ctx& c, int kb, int np, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy,
                  int y0, int32_t* perm, T* tmp, int* imap);
 
 // FP64-accurate product on the bf16 tensor cores (ozaki.cu); iscr holds

@@ -17,10 +17,14 @@
 // nothing needs clearing between calls.
 //
 // Set-up: host code cannot use the array's name as a device address (in host
-// code it is a stand-in object). The first call on each device, with that
-// device current, looks up the device address with cudaGetSymbolAddress and
-// caches it; that first call therefore must not happen while the stream is
-// being captured into a CUDA graph.
+// code it is a stand-in object). The first call with a handle of a given
+// device looks up that device's copy of the array with cudaGetSymbolAddress,
+// with the handle's device made current for the lookup (the caller's current
+// device is restored afterwards), and caches it per device; that first call
+// therefore must not happen while the stream is being captured into a CUDA
+// graph. The cache assumes the device's primary context lives as long as the
+// process: after cudaDeviceReset the cached address is stale, so a process
+// that resets a device must not call this entry point on it again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,17 +44,26 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
-// Device address of the static scratch on the current device (looked up once).
-int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return RQR_ERR_CUDA;
-  }
+// Device address of the static scratch on device `dev` (the handle's device,
+// whose stream runs the kernels), looked up once per device with that device
+// current; the caller's current device is restored.
+int scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return RQR_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return RQR_ERR_CUDA;
+    }
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return RQR_ERR_CUDA;
+    }
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return RQR_ERR_CUDA;
     }
@@ -124,7 +137,7 @@ int rqr_form_q_noalloc(rqr_handle_t h, int m, int n, int b, const void* F, int l
                                      : layout<float>(m, b, ncols, ow, ow2, op, cap);
   if (!fits) return RQR_ERR_SIZE;
   void* base = nullptr;
-  const int rc = scratch_address(&base);
+  const int rc = scratch_address(c.device, &base);
   if (rc != RQR_OK) return rc;
   cudaGetLastError();
   const int st = prec == RQR_FP64

@@ -10,9 +10,12 @@
 // device-scope atomic per CTA, no release phase), and the data exchanged
 // through global memory is reduced by every CTA (pivot winner) or by one CTA
 // per entry (panel sums) in a fixed order, so results do not depend on timing.
-// Waits are bounded by ~2 s of global time; a wait that runs out sets
-// RQR_ERR_TIMEOUT in the status word and every CTA returns (co-residency is
-// guaranteed by the cooperative launch, so this only guards against a defect).
+// Waits are bounded by the handle's wait limit (2 s of global time unless the
+// caller sets another); a wait that runs out sets RQR_ERR_TIMEOUT in the
+// status word and every CTA returns (co-residency is guaranteed by the
+// cooperative launch, so with the default limit this only guards against a
+// defect). A kernel launched after the status word was set returns at once:
+// the picks and panel values of an aborted step are never used.
 #include <algorithm>
 
 #include "common.cuh"
@@ -40,7 +43,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 // Arrival barrier on a counter that only grows: CTA arrivals of step s bring
 // it to C (s + 1). Thread 0 of every CTA publishes its CTA's writes with a
-// device-scope fence and one atomic, then spins (bounded by ~2 s of global
+// device-scope fence and one atomic, then spins (bounded by limit_ns of global
 // time) until every CTA has arrived; false when the wait ran out or another
 // CTA gave up.
 __device__ __forceinline__ uint64_t gtime_ns() {
@@ -49,7 +52,7 @@ __device__ __forceinline__ uint64_t gtime_ns() {
   return t;
 }
 
-__device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* status) {
+__device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* status, unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -59,7 +62,7 @@ __device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* s
     if (ld_acquire(count) < target) {
       const uint64_t t0 = gtime_ns();
       while (ld_acquire(count) < target) {
-        if (*(volatile int*)err || gtime_ns() - t0 > 2000000000ull) {
+        if (*(volatile int*)err || gtime_ns() - t0 > limit_ns) {
           atomicExch(err, 1);
           atomicCAS(status, 0, RQR_ERR_TIMEOUT);
           ok = 0;
@@ -85,6 +88,7 @@ struct PArgs {
   T* colbuf;    // [2][l + 2] column leaving the pivot position, its norm and reference norm
   GridSync* gs;
   int* status;
+  unsigned long long wait_ns;  // limit of each arrival wait
 };
 
 // Candidates compare by key: the bit pattern of a squared norm (>= 0) as a
@@ -129,6 +133,9 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   __shared__ T s_tau;
   __shared__ int s_win, s_pos;
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // an earlier step of this call failed: nothing here may be trusted (every
+  // CTA reads the same word before any of them can change it)
+  if (*(volatile int*)a.status != 0) return;
   const int lo = q * a.per, hi = min(a.np, lo + a.per), cnt = max(0, hi - lo);
   for (int e = tid; e < cnt * l; e += PT) {
     const int pl = e / l, r = e % l;
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
         a.colbuf[(size_t)par * LB + l + 1] = ref[s - lo];
       }
     }
-    if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status)) return;
+    if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status, a.wait_ns)) return;
     // ---- global winner (every CTA, identical order)
     long long cn = -1;
     int cp = 0x7fffffff, cq = 0;
@@ -341,6 +348,7 @@ struct QArgs {
   T* coef;    // [2][NCOEF + nc]
   GridSync* gs;
   int* status;
+  unsigned long long wait_ns;  // limit of each arrival wait
 };
 
 // Column totals of the CTA partials: CTA e adds entry e of all C partial
@@ -382,6 +390,10 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   __shared__ T s_coef[NCOEF];
   __shared__ T s_rd;  // 1 / d of the current reflector: one division per column, not one per row
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // an earlier step failed: leave the panel as it is (no CTA of this launch
+  // can set the word before every CTA has passed this point: the first
+  // exchange waits for all of them)
+  if (*(volatile int*)a.status != 0) return;
   const int RS = R | 1;  // odd column stride: a thread per column reads without bank conflicts
   const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
   T* total = a.coef;  // [nc + 1]
@@ -394,10 +406,10 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   // Exchange after the partials of column jn are published: totals, then the
   // coefficients of jn's reflector and w[c] = tau (x_jn,c + dot_c / d), c > jn.
   auto exchange = [&](int jn) -> bool {
-    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status)) return false;
+    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status, a.wait_ns)) return false;
     for (int e = q; e <= nc; e += C)
       if (e == 0 || e >= jn + 2) reduce_entry<T>(e, nc, a.part, total);
-    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status)) return false;
+    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status, a.wait_ns)) return false;
     const T* rb = a.rowbuf + (size_t)(jn & 1) * nc;
     if (tid == 0) {
       reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
@@ -533,7 +545,7 @@ bool panel_qr_persist(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* sc
   T* tail = coef + 2 * (size_t)(pnl::NCOEF + nc);
   GridSync* gs = reinterpret_cast<GridSync*>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
   cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  QArgs<T> a{mp, nc, R, P, ldp, tau, part, rowbuf, coef, gs, c.status};
+  QArgs<T> a{mp, nc, R, P, ldp, tau, part, rowbuf, coef, gs, c.status, c.wait_ns};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_panel_persist<T>, dim3(C), dim3(pnl::PT), args, smem, c.stream) !=
       cudaSuccess) {
@@ -589,7 +601,7 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
   T* colbuf = candcol + 2 * (size_t)C * l;
   int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)(l + 2) + 8);
   cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_k, cand_p, candcol, colbuf, gs, c.status};
+  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_k, cand_p, candcol, colbuf, gs, c.status, c.wait_ns};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_ypick_persist<T>, dim3(C), dim3(PT), args, smem, c.stream) !=
       cudaSuccess) {

@@ -225,9 +225,23 @@ __global__ void __launch_bounds__(YT) k_ypick_step(int j, YArgs a, const T* __re
 // emits (dst, src) pairs of the net permutation: imap[0] = count, then pairs.
 // Positions below kb map to their own slot; the at most kb others go through
 // an open-addressing hash table in shared memory, so the replay is O(kb).
+// When the status word is already set (a pivot step gave up, so picks may be
+// stale) or a pick lies outside [j, np), no swap is made: imap[0] = 0.
 constexpr int kMapHash = 2048;  // >= 4 kb for kb <= 512
-__global__ void k_build_map(int kb, const int* picks, int* imap) {
+__global__ void k_build_map(int kb, int np, const int* picks, int* imap, int* status) {
   extern __shared__ int sh[];
+  const bool failed = *(volatile int*)status != 0;  // set by an earlier kernel of the stream
+  int bad = 0;
+  for (int j = threadIdx.x; j < kb; j += blockDim.x)
+    if (picks[j] < j || picks[j] >= np) bad = 1;
+  bad = __syncthreads_or(bad);
+  if (failed || bad) {
+    if (threadIdx.x == 0) {
+      imap[0] = 0;
+      if (!failed) atomicCAS(status, 0, RQR_ERR_CUDA);
+    }
+    return;
+  }
   int* cont = sh;               // [kb] content of positions 0..kb-1
   int* hkey = sh + kb;          // [kMapHash] position, -1 = empty
   int* hval = hkey + kMapHash;  // [kMapHash] content
@@ -347,10 +361,10 @@ void ypick(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy, int* pi
 }
 
 template <typename T>
-void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy, int y0,
-                 int32_t* perm, T* tmp, int* imap) {
+void apply_swaps(const Ctx& c, int kb, int np, const int* picks, int m, T* A, int lda, int k0, int l, T* Y, int ldy,
+                 int y0, int32_t* perm, T* tmp, int* imap) {
   if (kb <= 0) return;
-  k_build_map<<<1, 256, sizeof(int) * ((size_t)kb + 2 * kMapHash), c.stream>>>(kb, picks, imap);
+  k_build_map<<<1, 256, sizeof(int) * ((size_t)kb + 2 * kMapHash), c.stream>>>(kb, np, picks, imap, c.status);
   T* tmpA = tmp;
   T* tmpY = tmpA + (size_t)m * 2 * kb;
   int32_t* tmpP = reinterpret_cast<int32_t*>(tmpY + (size_t)l * 2 * kb);
@@ -363,8 +377,8 @@ void apply_swaps(const Ctx& c, int kb, const int* picks, int m, T* A, int lda, i
 #define RQR_INST(T)                                                                                      \
   template size_t ypick_scratch_elems<T>(int, int, int, int);                                           \
   template void ypick<T>(const Ctx&, int, int, int, const T*, int, int*, T*);                             \
-  template void apply_swaps<T>(const Ctx&, int, const int*, int, T*, int, int, int, T*, int, int, int32_t*, T*, \
-                               int*);
+  template void apply_swaps<T>(const Ctx&, int, int, const int*, int, T*, int, int, int, T*, int, int, int32_t*, \
+                               T*, int*);
 RQR_INST(double)
 RQR_INST(float)
 #undef RQR_INST

@@ -41,6 +41,7 @@ struct rqr_handle_s {
   cudaStream_t stream;
   int* d_status;
   int64_t nlaunch;
+  unsigned long long wait_ns;  // grid-arrival wait limit of the persistent kernels
   RqrProfile prof;
   rqr::KernelTimer kt;
 };
@@ -48,10 +49,13 @@ struct rqr_handle_s {
 namespace {
 
 constexpr unsigned kMagic = 0x52515231u;  // "RQR1"
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
 
 bool valid(rqr_handle_t h) { return h && h->magic == kMagic; }
 
-rqr::Ctx make_ctx(rqr_handle_t h) { return rqr::Ctx{h->stream, h->sms, h->d_status, &h->nlaunch, &h->kt}; }
+rqr::Ctx make_ctx(rqr_handle_t h) {
+  return rqr::Ctx{h->stream, h->sms, h->d_status, &h->nlaunch, &h->kt, h->device, h->wait_ns};
+}
 
 // Scope of one phase: start/end events when profiling is on, launches and
 // algorithmic flops attributed to the phase.
@@ -267,7 +271,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
     }
     {
       Phase ph(h, RQR_PHASE_SWAP, 0.0);
-      apply_swaps<T>(c, b, w.picks, m, A, lda, k0, l, down ? w.Y : nullptr, l, k0, perm, w.swp, w.imap);
+      apply_swaps<T>(c, b, np, w.picks, m, A, lda, k0, l, down ? w.Y : nullptr, l, k0, perm, w.swp, w.imap);
     }
     // (d) panel QR + T. With the tensor-core products (emu) V is split into
     // its unit diagonal E and strictly lower part L, V = E + L: the products
@@ -548,6 +552,7 @@ int rqr_create(rqr_handle_t* h, void* stream) {
   if (!s) return RQR_ERR_CUDA;
   s->magic = kMagic;
   s->nlaunch = 0;
+  s->wait_ns = kDefaultWaitNs;
   s->stream = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
@@ -575,6 +580,12 @@ int rqr_destroy(rqr_handle_t h) {
 int rqr_set_stream(rqr_handle_t h, void* stream) {
   if (!valid(h)) return RQR_ERR_HANDLE;
   h->stream = static_cast<cudaStream_t>(stream);
+  return RQR_OK;
+}
+
+int rqr_set_wait_limit_ns(rqr_handle_t h, uint64_t ns) {
+  if (!valid(h)) return -1;
+  h->wait_ns = ns == 0 ? kDefaultWaitNs : (unsigned long long)ns;
   return RQR_OK;
 }
 

@@ -28,7 +28,8 @@ STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 3: "a
 FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 
 # every symbol declared in include/rqr.h
-EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_workspace_bytes", "rqrcp_factor", "rurv_factor",
+EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_set_wait_limit_ns", "rqr_workspace_bytes",
+           "rqrcp_factor", "rurv_factor",
            "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill",
            "rqr_philox_raw",
            "rqr_profile_enable", "rqr_profile_read", "rqr_profile_kernel_read", "rqr_version")
@@ -58,6 +59,7 @@ def load(path: str = SO_PATH):
         L.rqr_create.argtypes = [ctypes.POINTER(vp), vp]
         L.rqr_destroy.argtypes = [vp]
         L.rqr_set_stream.argtypes = [vp, vp]
+        L.rqr_set_wait_limit_ns.argtypes = [vp, u64]
         L.rqr_workspace_bytes.argtypes = [i, i, i, i, i, i, i, ctypes.POINTER(sz)]
         L.rqrcp_factor.argtypes = [vp, i, i, vp, i, i, i, u64, vp, i, vp, i, vp, i, i, vp, sz, ip]
         L.rurv_factor.argtypes = [vp, i, i, vp, i, i, i, i, i, u64, vp, vp, i, vp, i, vp, i, vp, i, vp, i, i, vp, sz,
@@ -103,6 +105,15 @@ def handle(device: torch.device | None = None) -> ctypes.c_void_p:
             _handles[dev] = h
     L.rqr_set_stream(h, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
     return h
+
+
+def set_wait_limit_ns(ns: int, device=None) -> None:
+    """Limit of the grid-arrival waits of the cooperative pivot and panel
+    kernels on this device's handle (0 restores the default of 2 s). A wait
+    that runs out ends the factorization with status 3 (timeout)."""
+    rc = load().rqr_set_wait_limit_ns(handle(device), int(ns))
+    if rc != 0:
+        raise RQRError(f"rqr_set_wait_limit_ns failed ({rc})")
 
 
 def colmajor(A: torch.Tensor) -> torch.Tensor:

@@ -82,3 +82,41 @@ def test_tc_matches_native_fp64_on_trailing_update_shape():
     rqr.gemm(Vd, W, Ad, alpha=-1.0, beta=1.0, emulated=True)
     ref = A22 - V @ (V.T @ A22)
     assert np.abs(host(Ad) - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+# op(B) larger than the library's plane budget for one launch (8 N K bf16
+# values > 512 Mi, i.e. N K > 64 Mi): the product runs over column chunks of
+# op(B) (a full chunk of 4096 columns and a ragged last one), each with long-K
+# split-K partial sums (K = 16384 is 128 windows of 128 K) and the reduction
+# kernel. These are the paths the 8192^2 and 16384^2 factorizations take.
+BIG = [(128, 4160, 16384, True, False), (136, 4200, 16000, False, True)]
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb", BIG)
+def test_tc_chunked_long_k_integer_exact(M, N, K, ta, tb):
+    assert 8 * N * K > 512 * 2 ** 20
+    r = np.random.default_rng(N + K)
+    A = r.integers(-2048, 2048, size=(M, K)).astype(np.float64)
+    B = r.integers(-2048, 2048, size=(K, N)).astype(np.float64)
+    Ad = dev(A.T) if ta else dev(A)
+    Bd = dev(B.T) if tb else dev(B)
+    C = host(rqr.gemm(Ad, Bd, ta=ta, tb=tb, emulated=True))
+    np.testing.assert_array_equal(C, A @ B)
+
+
+@pytest.mark.parametrize("M,N,K,ta,tb", BIG)
+def test_tc_chunked_long_k_within_fp64_bound(M, N, K, ta, tb):
+    r = np.random.default_rng(3 * N + K)
+    A = r.standard_normal((M, K)) * (10.0 ** r.uniform(-6, 6, size=(M, 1)))
+    B = r.standard_normal((K, N)) * (10.0 ** r.uniform(-6, 6, size=(1, N)))
+    C0 = r.standard_normal((M, N))
+    Ad = dev(A.T) if ta else dev(A)
+    Bd = dev(B.T) if tb else dev(B)
+    Cd = dev(C0)
+    rqr.gemm(Ad, Bd, Cd, ta=ta, tb=tb, alpha=-1.0, beta=1.0, emulated=True)
+    ref = C0 - A @ B
+    rowmax = np.abs(A).max(axis=1, keepdims=True)
+    bound = 1.5 * K * U * (rowmax @ np.abs(B).sum(axis=0, keepdims=True) / K + np.abs(A) @ np.abs(B)) \
+        + 4 * U * np.abs(ref) + 1e-300
+    err = np.abs(host(Cd) - ref)
+    assert np.all(err <= bound), float((err / bound).max())

@@ -238,14 +238,17 @@ def apply_q(F, T, b, X, transpose=False):
     return X
 
 
+@pytest.mark.parametrize("emulated", [False, True])
 @pytest.mark.parametrize("n,b,p", [(8192, 128, 8)])
-def test_rqrcp_full_size_spike(n, b, p):
+def test_rqrcp_full_size_spike(n, b, p, emulated):
     # Gaussian plus rank-200 spike at the full 8192 size: the oracle computes the
-    # first block (sampled outputs), properties cover the rest.
+    # first block (sampled outputs), properties cover the rest. emulated=True is
+    # the FP64X mode at a size where op(B) is split into column chunks and the
+    # long-K products run split-K on the tcgen05 kernel.
     A = inputs.torch_spike_matrix(n, seed=1505)
     G = inputs.torch_sketch_gaussian(1506, b + p, n)
     A0 = A.clone()
-    T, perm, info = rqr.rqrcp_factor(A, b, p, G=G)
+    T, perm, info = rqr.rqrcp_factor(A, b, p, G=G, emulated=emulated)
     torch.cuda.synchronize()
     assert info == 0
     permc = perm.cpu().numpy()
@@ -273,3 +276,30 @@ def test_rqrcp_full_size_spike(n, b, p):
     QtQx = apply_q(A, T, b, apply_q(A, T, b, X), transpose=True)
     assert (torch.linalg.norm(QtQx - X) / torch.linalg.norm(X)).item() <= 1e-13
     assert abs(torch.linalg.norm(R).item() / torch.linalg.norm(A0).item() - 1) <= 1e-12
+
+
+def test_wait_limit_timeout_then_recovery():
+    """A grid-arrival wait of the cooperative pivot/panel kernels that runs out
+    ends the call with RQR_ERR_TIMEOUT (3) instead of hanging, and the handle
+    stays usable. The limit is set to 1 ns on the handle, so the first wait of
+    ordinary work for a CTA that arrives before the others gives up: no kernel
+    is altered, nothing faults. Then the default limit is restored and the same
+    handle factors the same matrix correctly."""
+    m, n, b, p = 2048, 2048, 128, 8
+    A = inputs.a_fast(n, seed=21, m=m)
+    G = inputs.sketch_gaussian(22, b + p, m)
+    try:
+        rqr.set_wait_limit_ns(1)
+        Ad = dev(A)
+        T, perm, info = rqr.rqrcp_factor(Ad, b, p, G=dev(G))
+        torch.cuda.synchronize()
+        assert info == 3, info
+        # the swaps of an aborted step are skipped, so perm stays a permutation
+        assert sorted(perm.cpu().numpy().tolist()) == list(range(n))
+    finally:
+        rqr.set_wait_limit_ns(0)
+    F, T, perm, info = gpu_factor(A, b, p, G, DOWN)
+    assert info == 0
+    F0, T0, perm0, _ = oracle.rqrcp(A, b, p, G, max_blocks=2)
+    np.testing.assert_array_equal(perm[:2 * b], perm0[:2 * b])
+    check_bounds(A, F, T, perm, b)
