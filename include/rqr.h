@@ -33,12 +33,30 @@ extern "C" {
 
 typedef struct rqr_handle_s* rqr_handle_t;
 
-/* Arithmetic of the factorization (the `prec` argument). */
-#define RQR_FP64 0 /* every step in FP64 (A, T are double) */
-#define RQR_FP32 1 /* every step in FP32 (A, T are float) */
-#define RQR_FP64X 2 /* FP64 data and FP64 panel/pivot/T steps; the large products
-                       (sketch, trailing update, downdate, Gram) are FP64-accurate
-                       splittings onto the bf16 tensor cores (Ozaki scheme) */
+/* Arithmetic of the factorization (the `prec` argument).
+ * FP64: every step in FP64 on the FP64 pipe (A, G, T are double).
+ * FP32: A, G, T are float; the large products run on the tensor cores as
+ *   3xTF32 (FP32-level accuracy, FP32 accumulation), the rest in FP32.
+ * TF32, 3XBF16, 3XTF32 (mixed precision): A, G, T are double; the panel
+ *   Householder QR, its Gram matrix V^T V and T, the pivot steps on the
+ *   sketch and the small products stay in FP64, so Q = prod(I - V T V^T) is
+ *   orthogonal to FP64 rounding; the large products (sketch, trailing update,
+ *   sketch downdate; for the URV method also the power steps and the right
+ *   apply) run on the tcgen05 tensor cores with FP32 accumulation and
+ *   operands rounded to one TF32 value (TF32), to a bf16 hi + lo pair with
+ *   the products hi*hi + hi*lo + lo*hi (3XBF16, about 16 bits), or to a TF32
+ *   big + small pair with big*big + big*small + small*big (3XTF32, about FP32
+ *   accuracy). The residual ||AP - QR||/||A|| then follows the product
+ *   precision (of order 1e-3, 1e-5, 1e-6 at n = 16384).
+ * FP64X: FP64 data and FP64 panel/pivot/T steps; the large products
+ *   (sketch, trailing update, downdate, Gram) are FP64-accurate splittings
+ *   onto the bf16 tensor cores (Ozaki scheme): FP64-level residual. */
+#define RQR_FP64 0
+#define RQR_FP32 1
+#define RQR_TF32 2
+#define RQR_3XBF16 3
+#define RQR_3XTF32 4
+#define RQR_FP64X 5
 
 /* How the sketch follows the factorization from block to block (`sketch`). */
 #define RQR_SKETCH_DOWNDATE 0 /* draw G once, update Y = G X after each block */

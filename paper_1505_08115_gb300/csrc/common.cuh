@@ -122,6 +122,9 @@ template <typename T>
 void copy_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
 template <typename T>
 void set_mat(const Ctx& c, int r, int cols, T val, T* dst, int ldd);
+// dst (cols x r, ld ldd) = src (r x cols, ld lds)^T.
+template <typename T>
+void transpose_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
 
 // Explicit unit-lower-trapezoidal V (m' x kb, ld ldv) from the factored panel.
 template <typename T>
@@ -218,6 +221,19 @@ bool oztc_available();
 bool gemm_f64x_tc(const Ctx& c, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
                   const double* B, int ldb, double beta, double* C, int ldc, int* emax, uint16_t* pa, size_t pa_cap,
                   uint16_t* pb, size_t pb_cap, double* part, size_t part_cap);
+
+// Products of the mixed-precision modes (tcmix.cu): C = alpha op(A) op(B) +
+// beta C with operands rounded to TF32 / split into bf16 hi+lo / TF32
+// big+small (mode = RQR_TF32, RQR_3XBF16, RQR_3XTF32) and FP32 accumulation on
+// the tcgen05 tensor cores. pa, pb: scratch for the operand planes (bytes;
+// op(B) is processed in column chunks that fit pb). Returns false, with
+// nothing queued, when the tensor-map encoder is missing or op(A)'s planes do
+// not fit.
+size_t mix_plane_bytes(int mode, int rows, int K);
+template <typename T>
+bool gemm_mix_tc(const Ctx& c, int mode, bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda,
+                 const T* B, int ldb, T beta, T* C, int ldc, void* pa, size_t pa_bytes, void* pb, size_t pb_bytes,
+                 T* part, size_t part_cap);
 
 // ---------------------------------------------------------------- small SVD
 // One-sided Jacobi on the r x cols matrix M (FP64, overwritten by M J); Js

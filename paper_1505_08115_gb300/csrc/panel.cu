@@ -407,6 +407,23 @@ __global__ void k_copy_mat(int r, int cols, const T* __restrict__ s, int lds, T*
   }
 }
 
+// dst (cols x r) = src (r x cols)^T, 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(int r, int cols, const T* __restrict__ s, int lds,
+                                                   T* __restrict__ d, int ldd) {
+  __shared__ T tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int y = ty; y < 32; y += 8) {
+    const int i = i0 + tx, j = j0 + y;
+    if (i < r && j < cols) tile[y][tx] = s[i + (size_t)j * lds];
+  }
+  __syncthreads();
+  for (int y = ty; y < 32; y += 8) {
+    const int j = j0 + tx, i = i0 + y;
+    if (i < r && j < cols) d[j + (size_t)i * ldd] = tile[tx][y];
+  }
+}
+
 template <typename T>
 __global__ void k_set_mat(int r, int cols, T val, T* d, int ldd) {
   const int64_t n = (int64_t)r * cols;
@@ -564,6 +581,14 @@ template void gram_from_lower<double>(const Ctx&, int, const double*, int, doubl
 template void gram_from_lower<float>(const Ctx&, int, const float*, int, float*, int);
 
 template <typename T>
+void transpose_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd) {
+  if (r <= 0 || cols <= 0) return;
+  dim3 g(ceil_div(r, 32), ceil_div(cols, 32));
+  k_transpose<T><<<g, 256, 0, c.stream>>>(r, cols, src, lds, dst, ldd);
+  note_launch(c);
+}
+
+template <typename T>
 void copy_mat(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd) {
   if (r <= 0 || cols <= 0) return;
   k_copy_mat<T><<<grid1d((int64_t)r * cols, c.sms), 256, 0, c.stream>>>(r, cols, src, lds, dst, ldd);
@@ -606,6 +631,7 @@ void add_mat(const Ctx& c, int r, int cols, T alpha, const T* src, int lds, T* d
   template void qrcp_block<T>(const Ctx&, int, int, int, int, T*, int, int32_t*, T*, T*);                 \
   template void larft_tri<T>(const Ctx&, int, const T*, int, const T*, T*, int);                          \
   template void copy_mat<T>(const Ctx&, int, int, const T*, int, T*, int);                                \
+  template void transpose_mat<T>(const Ctx&, int, int, const T*, int, T*, int);                           \
   template void set_mat<T>(const Ctx&, int, int, T, T*, int);                                             \
   template void make_vx<T>(const Ctx&, int, int, const T*, int, T*, int);
 RQR_INST(double)

@@ -53,6 +53,11 @@ constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
 
 bool valid(rqr_handle_t h) { return h && h->magic == kMagic; }
 
+bool valid_prec(int prec) {
+  return prec == RQR_FP64 || prec == RQR_FP32 || prec == RQR_FP64X || prec == RQR_TF32 || prec == RQR_3XBF16 ||
+         prec == RQR_3XTF32;
+}
+
 rqr::Ctx make_ctx(rqr_handle_t h) {
   return rqr::Ctx{h->stream, h->sms, h->d_status, &h->nlaunch, &h->kt, h->device, h->wait_ns};
 }
@@ -102,10 +107,25 @@ struct RqrcpWs {
   rqr::TcScratch tc;
 };
 
-// Scratch of the tcgen05 FP64-accurate products (FP64X mode): exponent maxima,
-// digit planes of op(A) and of op(B) (op(B) is split in column chunks that fit
-// into at most kTcPlaneBudget bf16 values).
+// Scratch of the tensor-core products: exponent maxima (FP64X), the operand
+// planes of op(A) and of op(B) (op(B) is split in column chunks whose planes
+// fit into kTcPlaneBudget bf16 values, 1 GiB).
 constexpr size_t kTcPlaneBudget = (size_t)512 << 20;
+
+bool is_mixed(int prec) { return prec == RQR_TF32 || prec == RQR_3XBF16 || prec == RQR_3XTF32; }
+
+// Tensor-core product mode of a factorization precision: FP64X (digit
+// planes), a mixed mode, 3XTF32 for FP32 data, or 0 (FP64: no tensor cores).
+int tc_mode(int prec) {
+  if (prec == RQR_FP64X || is_mixed(prec)) return prec;
+  return prec == RQR_FP32 ? RQR_3XTF32 : 0;
+}
+
+// Operand planes of `rows` rows of length K, in bf16 units (2 bytes).
+size_t tc_plane_units(int mode, int rows, int K) {
+  if (mode == RQR_FP64X) return rqr::oztc_plane_elems(rows, K);
+  return (rqr::mix_plane_bytes(mode, rows, K) + 1) / 2;
+}
 
 void carve_tc(rqr::Carver& cv, size_t emax_elems, size_t pa_elems, size_t pb_elems, rqr::TcScratch& s) {
   s.emax = cv.take<int>(emax_elems);
@@ -115,44 +135,55 @@ void carve_tc(rqr::Carver& cv, size_t emax_elems, size_t pa_elems, size_t pb_ele
   s.pb = cv.take<uint16_t>(pb_elems);
 }
 
-// Scratch of one FP64X product through rqr_gemm.
-void gemm_tc_carve(rqr::Carver& cv, int M, int N, int K, rqr::TcScratch& s) {
+// Scratch of one tensor-core product through rqr_gemm (mode RQR_FP64X or a
+// mixed mode): op(A)'s planes whole, op(B)'s in column chunks of at least one
+// output tile (256 columns) within the plane budget.
+void gemm_tc_carve(rqr::Carver& cv, int mode, int M, int N, int K, rqr::TcScratch& s) {
   M = std::max(M, 1);
   N = std::max(N, 1);
   K = std::max(K, 1);
-  carve_tc(cv, (size_t)M + N + 64, rqr::oztc_plane_elems(M, K),
-           std::min(rqr::oztc_plane_elems(N, K), std::max(kTcPlaneBudget, rqr::oztc_plane_elems(64, K))), s);
+  carve_tc(cv, mode == RQR_FP64X ? (size_t)M + N + 64 : 1, tc_plane_units(mode, M, K),
+           std::min(tc_plane_units(mode, N, K), std::max(kTcPlaneBudget, tc_plane_units(mode, 256, K))), s);
 }
 
-// Dense product of the method: native precision, or (FP64 with emu) the
-// FP64-accurate bf16 tensor-core splitting of ozaki.cu for products large
-// enough to pay for the splitting.
+// Dense product of the method: native precision; or, for products large
+// enough to pay for the operand splitting, on the tensor cores: the
+// FP64-accurate bf16 digit splitting (mode RQR_FP64X: tcgen05 kernel of
+// oztc.cu, mma.sync fallback of ozaki.cu), or a mixed-precision mode with FP32
+// accumulation (RQR_TF32, RQR_3XBF16, RQR_3XTF32: tcmix.cu).
 template <typename T>
 struct Gemm {
   const rqr::Ctx& c;
-  bool emu;
+  int mode;  // tc_mode() of the factorization, 0 = native only
   int* iscr;
   T* part;
   size_t cap;
-  const rqr::TcScratch* tc;  // null: the mma.sync splitting only
+  const rqr::TcScratch* tc;  // null: no tensor-core scratch (FP64X: the mma.sync splitting only)
   void operator()(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, const T* B, int ldb, T beta,
                   T* C, int ldc) const {
-    if constexpr (sizeof(T) == 8) {
-      if (emu && (double)M * N * K >= 4.0e6 && M >= 16 && N >= 16 && K >= 16) {
-        if (tc && tc->pa &&
-            rqr::gemm_f64x_tc(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tc->emax, tc->pa, tc->pa_cap,
-                              tc->pb, tc->pb_cap, part, cap))
+    const bool big = (double)M * N * K >= 4.0e6 && M >= 16 && N >= 16 && K >= 16;
+    if (mode && big) {
+      if constexpr (sizeof(T) == 8) {
+        if (mode == RQR_FP64X) {
+          if (tc && tc->pa &&
+              rqr::gemm_f64x_tc(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tc->emax, tc->pa,
+                                tc->pa_cap, tc->pb, tc->pb_cap, part, cap))
+            return;
+          rqr::gemm_f64x(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, iscr, part, cap);
           return;
-        rqr::gemm_f64x(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, iscr, part, cap);
-        return;
+        }
       }
+      if (mode != RQR_FP64X && tc && tc->pa &&
+          rqr::gemm_mix_tc<T>(c, mode, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tc->pa, 2 * tc->pa_cap,
+                              tc->pb, 2 * tc->pb_cap, part, cap))
+        return;
     }
     rqr::gemm<T>(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, part, cap);
   }
 };
 
 template <typename T>
-size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs<T>& w, bool tc = false) {
+size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs<T>& w, int tcm = 0) {
   const int l = b + p;
   w.Y = cv.take<T>((size_t)l * std::max(n, 1));
   w.Gc = cv.take<T>((size_t)l * std::max(m, 1));
@@ -173,14 +204,14 @@ size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs
   w.iscr = cv.take<int>(rqr::ozaki_scratch_elems(std::max(m, l), std::max(n, m)));
   w.pers = cv.take<char>(rqr::ypick_persist_scratch_bytes(l, std::max(n, 1), sms));
   w.tc = rqr::TcScratch{};
-  if (tc) {
+  if (tcm) {
     // largest op(A): G (l x m) or V^T (b x m') with long K, V (m' x b) with K = b;
     // largest op(B): A (n columns of length m), chunked, or short-K operands
     const int lb = std::max(l, b), mm = std::max(m, 1), nn = std::max(n, 1);
-    const size_t pa = std::max(rqr::oztc_plane_elems(lb, mm), rqr::oztc_plane_elems(mm, lb));
-    const size_t pb = std::max(rqr::oztc_plane_elems(std::max(nn, mm), lb),
-                               std::min(rqr::oztc_plane_elems(nn, mm), kTcPlaneBudget));
-    carve_tc(cv, (size_t)mm + nn + lb + 64, pa, pb, w.tc);
+    const size_t pa = std::max(tc_plane_units(tcm, lb, mm), tc_plane_units(tcm, mm, lb));
+    const size_t pb = std::max(tc_plane_units(tcm, std::max(nn, mm), lb),
+                               std::min(tc_plane_units(tcm, nn, mm), kTcPlaneBudget));
+    carve_tc(cv, tcm == RQR_FP64X ? (size_t)mm + nn + lb + 64 : 1, pa, pb, w.tc);
   }
   return cv.used;
 }
@@ -213,15 +244,18 @@ int finish(rqr_handle_t h, int* info) {
 
 template <typename T>
 int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64_t seed, const T* G, int ldg, T* Tm,
-               int ldt, int32_t* perm, int sketch, bool emu, void* work, size_t lwork, int* info) {
+               int ldt, int32_t* perm, int sketch, int prec, void* work, size_t lwork, int* info) {
   using namespace rqr;
   const int l = b + p;
+  const int tcm = tc_mode(prec);
+  // FP64X splits V into its unit diagonal and strictly lower part (below)
+  const bool emu = prec == RQR_FP64X;
   Carver cv{static_cast<char*>(work), lwork, 0, false};
   RqrcpWs<T> w;
-  carve_rqrcp<T>(cv, m, n, b, p, h->sms, w, emu);
+  carve_rqrcp<T>(cv, m, n, b, p, h->sms, w, tcm);
   if (!cv.ok()) return RQR_ERR_WORKSPACE;
   Ctx c = make_ctx(h);
-  const Gemm<T> mm{c, emu, w.iscr, w.part, w.part_cap, emu ? &w.tc : nullptr};
+  const Gemm<T> mm{c, tcm, w.iscr, w.part, w.part_cap, tcm ? &w.tc : nullptr};
   cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
   if (n == 0) return finish(h, info);
   const bool down = sketch == RQR_SKETCH_DOWNDATE;
@@ -369,11 +403,13 @@ int form_q_impl(rqr_handle_t h, int m, int n, int b, const T* F, int ldf, const 
 
 struct RurvWs {
   double *Z, *Qz, *Wm, *Qw, *Vx, *gram, *Tz, *W1, *Mj, *Jm, *Js, *sv, *Zr, *P1, *P2, *W, *W2, *tau, *part, *pscr;
-  int *order, *flags;
+  double *Vl, *Tt;  // tensor-core modes: strictly lower part of V (FP64X), transposed products
+  int *order, *flags, *iscr;
   size_t part_cap;
+  rqr::TcScratch tc;
 };
 
-size_t carve_rurv(rqr::Carver& cv, int m, int n, int b, int p, int sms, RurvWs& w) {
+size_t carve_rurv(rqr::Carver& cv, int m, int n, int b, int p, int sms, RurvWs& w, int tcm = 0) {
   const int l = b + p;
   const size_t mm = std::max(m, 1), nn = std::max(n, 1), mx = std::max(mm, nn);
   w.Z = cv.take<double>(nn * l);
@@ -399,6 +435,21 @@ size_t carve_rurv(rqr::Carver& cv, int m, int n, int b, int p, int sms, RurvWs& 
   w.pscr = cv.take<double>(rqr::panel_scratch_elems<double>((int)mx, l, sms));
   w.order = cv.take<int>((size_t)l);
   w.flags = cv.take<int>(8);
+  w.Vl = w.Tt = nullptr;
+  w.iscr = nullptr;
+  w.tc = rqr::TcScratch{};
+  if (tcm) {
+    // op(A) of every tensor-core product is one of the thin factors (at most
+    // max(l, b) rows or columns of length max(m, n)); the large matrix is op(B)
+    const int lb = std::max(l, b);
+    w.Vl = cv.take<double>(mx * b);
+    w.Tt = cv.take<double>(mx * lb);
+    w.iscr = cv.take<int>(rqr::ozaki_scratch_elems((int)std::max<size_t>(mx, l), (int)mx));
+    const size_t pa = std::max(tc_plane_units(tcm, lb, (int)mx), tc_plane_units(tcm, (int)mx, lb));
+    const size_t pb = std::max(tc_plane_units(tcm, (int)mx, lb), std::min(tc_plane_units(tcm, (int)mx, (int)mx),
+                                                                         kTcPlaneBudget));
+    carve_tc(cv, tcm == RQR_FP64X ? 2 * mx + lb + 64 : 1, pa, pb, w.tc);
+  }
   return cv.used;
 }
 
@@ -417,14 +468,29 @@ void form_thin_q(const rqr::Ctx& c, int r, int cc, int kq, const double* F, int 
 
 int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, int q, int k, uint64_t seed,
               const double* G, double* TU, int ldtu, double* WV, int ldwv, double* TV, int ldtv, double* DU, int lddu,
-              double* DV, int lddv, void* work, size_t lwork, int* info) {
+              double* DV, int lddv, int prec, void* work, size_t lwork, int* info) {
   using namespace rqr;
   const int l = b + p;
+  const int tcm = tc_mode(prec);
+  const bool emu = prec == RQR_FP64X;  // V = E + L split of the FP64X products (see rqrcp_impl)
   Carver cv{static_cast<char*>(work), lwork, 0, false};
   RurvWs w;
-  carve_rurv(cv, m, n, b, p, h->sms, w);
+  carve_rurv(cv, m, n, b, p, h->sms, w, tcm);
   if (!cv.ok()) return RQR_ERR_WORKSPACE;
   Ctx c = make_ctx(h);
+  const Gemm<double> mm{c, tcm, w.iscr, w.part, w.part_cap, tcm ? &w.tc : nullptr};
+  // C (M x N) = op(A) op(B) with a large op(A): the tensor-core kernels need
+  // op(A)'s planes whole, so they compute C^T = op(B)^T op(A)^T (the large
+  // matrix becomes op(B), split in column chunks) and the result is transposed.
+  auto mm_t = [&](bool ta, bool tb, int M, int N, int K, const double* Am, int ldam, const double* Bm, int ldbm,
+                  double* Cm, int ldcm) {
+    if (!tcm) {
+      gemm<double>(c, ta, tb, M, N, K, 1.0, Am, ldam, Bm, ldbm, 0.0, Cm, ldcm, w.part, w.part_cap);
+      return;
+    }
+    mm(!tb, !ta, N, M, K, 1.0, Bm, ldbm, Am, ldam, 0.0, w.Tt, N);
+    transpose_mat<double>(c, N, M, w.Tt, N, Cm, ldcm);
+  };
   cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
   if (n == 0) return finish(h, info);
   set_mat<double>(c, b, n, 0.0, TU, ldtu);
@@ -447,16 +513,16 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
         gauss_fill_2d<double>(c, seed, (uint64_t)blk, l, mp, w.Qw, l);
         Gi = w.Qw;
       }
-      gemm<double>(c, true, true, np, l, mp, 1.0, X, lda, Gi, l, 0.0, w.Z, np, w.part, w.part_cap);
+      mm_t(true, true, np, l, mp, X, lda, Gi, l, w.Z, np);
       for (int t = 0; t < q; ++t) {
         const int kz = std::min(np, zc);
         panel_qr<double>(c, np, zc, w.Z, np, w.tau, w.pscr);
         form_thin_q(c, np, zc, kz, w.Z, np, w.tau, w, w.Qz, np);
-        gemm<double>(c, false, false, mp, kz, np, 1.0, X, lda, w.Qz, np, 0.0, w.Wm, mp, w.part, w.part_cap);
+        mm_t(false, false, mp, kz, np, X, lda, w.Qz, np, w.Wm, mp);
         const int kw = std::min(mp, kz);
         panel_qr<double>(c, mp, kz, w.Wm, mp, w.tau, w.pscr);
         form_thin_q(c, mp, kz, kw, w.Wm, mp, w.tau, w, w.Qw, mp);
-        gemm<double>(c, true, false, np, kw, mp, 1.0, X, lda, w.Qw, mp, 0.0, w.Z, np, w.part, w.part_cap);
+        mm_t(true, false, np, kw, mp, X, lda, w.Qw, mp, w.Z, np);
         zc = kw;
       }
     }
@@ -485,9 +551,19 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
       // A(0:m, k0:n) <- A(0:m, k0:n) (I - W TS W^T), all m rows (Fig. blockRRQR)
       Phase ph(h, RQR_PHASE_RIGHT, 4.0 * m * (double)np * bi);
       double* Ak = A + (size_t)k0 * lda;
-      gemm<double>(c, false, false, m, bi, np, 1.0, Ak, lda, w.Vx, np, 0.0, w.P1, m, w.part, w.part_cap);
-      gemm<double>(c, false, false, m, bi, bi, 1.0, w.P1, m, TS, ldtv, 0.0, w.P2, m, w.part, w.part_cap);
-      gemm<double>(c, false, true, m, np, bi, -1.0, w.P2, m, w.Vx, np, 1.0, Ak, lda, w.part, w.part_cap);
+      if (!emu) {
+        mm_t(false, false, m, bi, np, Ak, lda, w.Vx, np, w.P1, m);
+        gemm<double>(c, false, false, m, bi, bi, 1.0, w.P1, m, TS, ldtv, 0.0, w.P2, m, w.part, w.part_cap);
+        mm(false, true, m, np, bi, -1.0, w.P2, m, w.Vx, np, 1.0, Ak, lda);
+      } else {
+        // W = E + L (unit diagonal E = [I; 0], strictly lower L), as in the left update
+        make_vlow<double>(c, np, bi, w.Vx, np, w.Vl, np);
+        mm_t(false, false, m, bi, np, Ak, lda, w.Vl, np, w.P1, m);                 // A L
+        add_mat<double>(c, m, bi, 1.0, Ak, lda, w.P1, m);                           // + A E
+        gemm<double>(c, false, false, m, bi, bi, 1.0, w.P1, m, TS, ldtv, 0.0, w.P2, m, w.part, w.part_cap);
+        mm(false, true, m, np, bi, -1.0, w.P2, m, w.Vl, np, 1.0, Ak, lda);          // - P2 L^T
+        add_mat<double>(c, m, bi, -1.0, w.P2, m, Ak, lda);                          // - P2 E^T
+      }
     }
     double* Tb = TU + (size_t)k0 * ldtu;
     {
@@ -501,9 +577,18 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
     if (n2 > 0) {
       Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * bi);
       double* A2 = A + k0 + (size_t)(k0 + bi) * lda;
-      gemm<double>(c, true, false, bi, n2, mp, 1.0, w.Vx, mp, A2, lda, 0.0, w.W, bi, w.part, w.part_cap);
-      gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
-      gemm<double>(c, false, false, mp, n2, bi, -1.0, w.Vx, mp, w.W2, bi, 1.0, A2, lda, w.part, w.part_cap);
+      if (!emu) {
+        mm(true, false, bi, n2, mp, 1.0, w.Vx, mp, A2, lda, 0.0, w.W, bi);
+        gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
+        mm(false, false, mp, n2, bi, -1.0, w.Vx, mp, w.W2, bi, 1.0, A2, lda);
+      } else {
+        make_vlow<double>(c, mp, bi, X, lda, w.Vl, mp);
+        copy_mat<double>(c, bi, n2, A2, lda, w.W, bi);                             // E^T A2
+        mm(true, false, bi, n2, mp, 1.0, w.Vl, mp, A2, lda, 1.0, w.W, bi);         // + L^T A2
+        gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
+        mm(false, false, mp, n2, bi, -1.0, w.Vl, mp, w.W2, bi, 1.0, A2, lda);      // - L W2
+        add_mat<double>(c, bi, n2, -1.0, w.W2, bi, A2, lda);                        // - E W2
+      }
     }
     if (DU && DV) {
       // Sec. 6.2 (Fig. blockRRQR): R11 = U' D Vt^T; A(0:k0, block) <- A(0:k0, block) Vt,
@@ -594,7 +679,7 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
   if (n < 0 || n > m) return -2;
   if (b < 1 || b > 512) return -3;
   if (p < 0) return -4;
-  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -6;
+  if (!valid_prec(prec)) return -6;
   if (sketch != RQR_SKETCH_DOWNDATE && sketch != RQR_SKETCH_RESAMPLE) return -7;
   if (!bytes) return -8;
   int dev = 0, sms = rqr::kNumSMs;
@@ -602,15 +687,15 @@ int rqr_workspace_bytes(int m, int n, int b, int p, int q, int prec, int sketch,
   cudaGetLastError();
   rqr::Carver cv{nullptr, 0, 0, true};
   if (q >= 0) {
-    if (prec != RQR_FP64) return -6;
+    if (prec == RQR_FP32) return -6;
     RurvWs w;
-    carve_rurv(cv, m, n, b, p, sms, w);
+    carve_rurv(cv, m, n, b, p, sms, w, tc_mode(prec));
   } else if (prec != RQR_FP32) {
     RqrcpWs<double> w;
-    carve_rqrcp<double>(cv, m, n, b, p, sms, w, prec == RQR_FP64X);
+    carve_rqrcp<double>(cv, m, n, b, p, sms, w, tc_mode(prec));
   } else {
     RqrcpWs<float> w;
-    carve_rqrcp<float>(cv, m, n, b, p, sms, w);
+    carve_rqrcp<float>(cv, m, n, b, p, sms, w, tc_mode(prec));
   }
   *bytes = cv.used + 256;
   return RQR_OK;
@@ -629,16 +714,16 @@ int rqrcp_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, u
   if (!T && n > 0) return -11;
   if (ldt < b) return -12;
   if (!perm && n > 0) return -13;
-  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -14;
+  if (!valid_prec(prec)) return -14;
   if (sketch != RQR_SKETCH_DOWNDATE && sketch != RQR_SKETCH_RESAMPLE) return -15;
   if (!work && n > 0) return -16;
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -16;
   cudaGetLastError();
   if (prec != RQR_FP32)
     return rqrcp_impl<double>(h, m, n, static_cast<double*>(A), lda, b, p, seed, static_cast<const double*>(G), ldg,
-                              static_cast<double*>(T), ldt, perm, sketch, prec == RQR_FP64X, work, lwork, info);
+                              static_cast<double*>(T), ldt, perm, sketch, prec, work, lwork, info);
   return rqrcp_impl<float>(h, m, n, static_cast<float*>(A), lda, b, p, seed, static_cast<const float*>(G), ldg,
-                           static_cast<float*>(T), ldt, perm, sketch, false, work, lwork, info);
+                           static_cast<float*>(T), ldt, perm, sketch, prec, work, lwork, info);
 }
 
 int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, int q, int k, uint64_t seed,
@@ -661,13 +746,13 @@ int rurv_factor(rqr_handle_t h, int m, int n, void* A, int lda, int b, int p, in
   if ((DU == nullptr) != (DV == nullptr)) return DU ? -20 : -18;
   if (DU && lddu < b) return -19;
   if (DV && lddv < b) return -21;
-  if (prec != RQR_FP64) return -22;
+  if (!valid_prec(prec) || prec == RQR_FP32) return -22;
   if (!work && n > 0) return -23;
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -23;
   cudaGetLastError();
   return rurv_impl(h, m, n, static_cast<double*>(A), lda, b, p, q, k, seed, static_cast<const double*>(G),
                    static_cast<double*>(TU), ldtu, static_cast<double*>(WV), ldwv, static_cast<double*>(TV), ldtv,
-                   static_cast<double*>(DU), lddu, static_cast<double*>(DV), lddv, work, lwork, info);
+                   static_cast<double*>(DU), lddu, static_cast<double*>(DV), lddv, prec, work, lwork, info);
 }
 
 int rqr_form_q(rqr_handle_t h, int m, int n, int b, const void* F, int ldf, const void* T, int ldt, void* Q, int ldq,
@@ -783,7 +868,7 @@ int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, double* b
 int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, double alpha, const void* A, int lda,
              const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork) {
   if (!valid(h)) return -1;
-  if (prec != RQR_FP64 && prec != RQR_FP32 && prec != RQR_FP64X) return -2;
+  if (!valid_prec(prec)) return -2;
   if (M < 0) return -5;
   if (N < 0) return -6;
   if (K < 0) return -7;
@@ -805,13 +890,26 @@ int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, doub
     float* part = cv.take<float>(cap);
     rqr::gemm<float>(c, ta != 0, tb != 0, M, N, K, (float)alpha, static_cast<const float*>(A), lda,
                      static_cast<const float*>(B), ldb, (float)beta, static_cast<float*>(C), ldc, part, cap);
+  } else if (is_mixed(prec)) {
+    const size_t cap = gemm_cap(h->sms);
+    double* part = cv.take<double>(cap);
+    rqr::TcScratch tc{};
+    gemm_tc_carve(cv, prec, M, N, K, tc);
+    if (M > 0 && N > 0 && K > 0 &&
+        rqr::gemm_mix_tc<double>(c, prec, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
+                                 static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, tc.pa,
+                                 2 * tc.pa_cap, tc.pb, 2 * tc.pb_cap, part, cap))
+      return finish(h, nullptr);
+    // no tensor-map encoder (or an empty product): the FP64 product
+    rqr::gemm<double>(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
+                      static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, part, cap);
   } else {
     const size_t cap = gemm_cap(h->sms);
     double* part = cv.take<double>(cap);
     int* iscr = cv.take<int>(rqr::ozaki_scratch_elems(M, N));
     rqr::TcScratch tc{};
-    if (prec == RQR_FP64X) gemm_tc_carve(cv, M, N, K, tc);
-    const Gemm<double> mm{c, prec == RQR_FP64X, iscr, part, cap, prec == RQR_FP64X ? &tc : nullptr};
+    if (prec == RQR_FP64X) gemm_tc_carve(cv, prec, M, N, K, tc);
+    const Gemm<double> mm{c, prec == RQR_FP64X ? RQR_FP64X : 0, iscr, part, cap, prec == RQR_FP64X ? &tc : nullptr};
     if (prec == RQR_FP64X && M > 0 && N > 0 && K > 0) {
       if (!rqr::gemm_f64x_tc(c, ta != 0, tb != 0, M, N, K, alpha, static_cast<const double*>(A), lda,
                              static_cast<const double*>(B), ldb, beta, static_cast<double*>(C), ldc, tc.emax, tc.pa,
@@ -827,18 +925,22 @@ int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, doub
 
 int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes) {
   if (!bytes) return -5;
-  (void)K;
+  if (!valid_prec(prec)) return -1;
   int dev = 0, sms = rqr::kNumSMs;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
   rqr::Carver cv{nullptr, 0, 0, true};
   if (prec == RQR_FP32) cv.take<float>(gemm_cap(sms));
-  else {
+  else if (is_mixed(prec)) {
+    cv.take<double>(gemm_cap(sms));
+    rqr::TcScratch tc{};
+    gemm_tc_carve(cv, prec, M, N, K, tc);
+  } else {
     cv.take<double>(gemm_cap(sms));
     cv.take<int>(rqr::ozaki_scratch_elems(std::max(M, 0), std::max(N, 0)));
     if (prec == RQR_FP64X) {
       rqr::TcScratch tc{};
-      gemm_tc_carve(cv, M, N, K, tc);
+      gemm_tc_carve(cv, prec, M, N, K, tc);
     }
   }
   *bytes = cv.used;

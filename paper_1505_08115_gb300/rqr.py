@@ -20,7 +20,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "librqr.so")
 
-FP64, FP32, FP64X = 0, 1, 2
+FP64, FP32, TF32, BF16X3, TF32X3, FP64X = 0, 1, 2, 3, 4, 5
+# names accepted by the prec= arguments (include/rqr.h: RQR_FP64 ... RQR_FP64X)
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "3xbf16": BF16X3, "3xtf32": TF32X3, "fp64x": FP64X}
 SKETCH_DOWNDATE, SKETCH_RESAMPLE = 0, 1
 STATUS = {0: "ok", 1: "cuda error", 2: "non-finite value in a panel norm", 3: "a bounded wait in a kernel ran out",
           4: "workspace too small", 5: "unsupported combination", 6: "invalid handle",
@@ -132,7 +134,18 @@ def _ld(A: torch.Tensor) -> int:
     return max(A.stride(1), max(1, m)) if n > 0 else max(1, m)
 
 
-def _prec(dtype, emulated: bool = False) -> int:
+def _prec(dtype, emulated: bool = False, prec=None) -> int:
+    """Precision code for the C ABI. prec (a name of PRECISIONS or a code)
+    overrides the default of the dtype: FP64 (FP64X with emulated=True) for
+    float64 data, FP32 for float32. The mixed modes take float64 data."""
+    if prec is not None:
+        code = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        if code not in PRECISIONS.values():
+            raise RQRError(f"unknown precision {prec!r}")
+        want = torch.float32 if code == FP32 else torch.float64
+        if dtype != want:
+            raise RQRError(f"precision {prec!r} takes {want} data, got {dtype}")
+        return code
     if dtype == torch.float64:
         return FP64X if emulated else FP64
     if dtype == torch.float32:
@@ -154,17 +167,19 @@ def _ptr(t):
 
 def rqrcp_factor(A: torch.Tensor, b: int, p: int, seed: int = 1505, G: torch.Tensor | None = None,
                  sketch: int = SKETCH_DOWNDATE, T: torch.Tensor | None = None, perm: torch.Tensor | None = None,
-                 work: torch.Tensor | None = None, check: bool = True, emulated: bool = False):
+                 work: torch.Tensor | None = None, check: bool = True, emulated: bool = False, prec=None):
     """Randomized blocked QRCP in place on A (column-major, on the GPU).
 
     Returns (T, perm, info); A holds R above the diagonal and the Householder
     vectors below. With check=False the call does not wait for the GPU and
     info is None. emulated=True (FP64 only) runs the large products as
-    FP64-accurate bf16 tensor-core splittings (RQR_FP64X)."""
+    FP64-accurate bf16 tensor-core splittings (RQR_FP64X); prec="tf32",
+    "3xbf16" or "3xtf32" runs them in that mixed precision with FP32
+    accumulation (float64 data; panel, T and pivots in FP64)."""
     _require_cuda(A)
     m, n = A.shape
     lda = _ld(A)
-    prec = _prec(A.dtype, emulated)
+    prec = _prec(A.dtype, emulated, prec)
     if T is None:
         T = empty_colmajor(b, n, A.dtype, A.device)
     if perm is None:
@@ -189,12 +204,15 @@ def rqrcp_factor(A: torch.Tensor, b: int, p: int, seed: int = 1505, G: torch.Ten
 
 def rurv_factor(A: torch.Tensor, b: int, p: int, q: int, k: int = 0, seed: int = 1505,
                 G: torch.Tensor | None = None, work: torch.Tensor | None = None, check: bool = True,
-                diag: bool = False):
+                diag: bool = False, emulated: bool = False, prec=None):
     """Blocked QR with orthonormal pivots. Returns (TU, WV, TV, info), or with
-    diag=True (diagonal blocks diagonalised, Sec. 6.2) (TU, WV, TV, DU, DV, info)."""
+    diag=True (diagonal blocks diagonalised, Sec. 6.2) (TU, WV, TV, DU, DV, info).
+    float64 data; emulated=True or prec="fp64x"/"tf32"/"3xbf16"/"3xtf32" run
+    the large products (power steps, right apply, trailing update) on the
+    tensor cores as in rqrcp_factor."""
     _require_cuda(A)
     m, n = A.shape
-    prec = _prec(A.dtype)
+    prec = _prec(A.dtype, emulated, prec)
     TU = empty_colmajor(b, n, A.dtype, A.device)
     TV = empty_colmajor(b, n, A.dtype, A.device)
     WV = empty_colmajor(n, n, A.dtype, A.device)
@@ -233,14 +251,15 @@ def form_q(F: torch.Tensor, T: torch.Tensor, b: int, ncols: int | None = None, w
 
 
 def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, ta: bool = False, tb: bool = False,
-         alpha: float = 1.0, beta: float = 0.0, emulated: bool = False) -> torch.Tensor:
+         alpha: float = 1.0, beta: float = 0.0, emulated: bool = False, prec=None) -> torch.Tensor:
     """C = alpha op(A) op(B) + beta C through the library's product kernels
-    (column-major tensors; FP64 DMMA, FP32 FFMA, or emulated FP64)."""
+    (column-major tensors; FP64 DMMA, FP32 FFMA, emulated FP64, or a mixed
+    mode on float64 data: prec="tf32", "3xbf16", "3xtf32")."""
     _require_cuda(A)
     M = A.shape[1] if ta else A.shape[0]
     K = A.shape[0] if ta else A.shape[1]
     N = B.shape[0] if tb else B.shape[1]
-    prec = _prec(A.dtype, emulated)
+    prec = _prec(A.dtype, emulated, prec)
     if C is None:
         C = empty_colmajor(M, N, A.dtype, A.device)
         beta = 0.0

@@ -69,7 +69,7 @@ def test_workspace_bytes_argument_codes():
     bad = [((-1, 0, 8, 2, -1, 0, 0), 1), ((10, 11, 8, 2, -1, 0, 0), 2), ((10, -1, 8, 2, -1, 0, 0), 2),
            ((10, 10, 0, 2, -1, 0, 0), 3), ((10, 10, 513, 2, -1, 0, 0), 3), ((10, 10, 8, -1, -1, 0, 0), 4),
            ((10, 10, 8, 2, -1, 7, 0), 6), ((10, 10, 8, 2, -1, 0, 5), 7),
-           ((10, 10, 8, 2, 1, 1, 0), 6), ((10, 10, 8, 2, 1, 2, 0), 6)]  # the URV method is FP64 only
+           ((10, 10, 8, 2, -1, 6, 0), 6), ((10, 10, 8, 2, 1, 1, 0), 6)]  # the URV method takes FP64 data
     for args, pos in bad:
         assert _ws(L, *args)[0] == -pos, args
     assert L.rqr_workspace_bytes(10, 10, 8, 2, -1, 0, 0, None) == -8
@@ -78,16 +78,24 @@ def test_workspace_bytes_argument_codes():
 
 def test_workspace_bytes_sizes():
     """The sizes the data layout states: at n = 16384, b = 128, p = 8 about
-    0.2 GB in FP64 and 1.3 GB with the FP64X digit planes; FP32 half of FP64;
+    0.2 GB in FP64 and 1.3 GB with the FP64X digit planes (the op(B) planes
+    capped at 1 GiB per chunk); FP32 half of FP64 plus its 3xTF32 planes
+    (8 bytes per element, chunk capped at 1 GiB); the mixed modes FP64's
+    buffers plus planes of 4 (TF32, 3xBF16) or 8 (3xTF32) bytes per element;
     the resampled sketch needs no more than the downdated one."""
     from paper_1505_08115_gb300 import rqr
     L = rqr.load()
-    rc, w64 = _ws(L, 16384, 16384, 128, 8, prec=0)
+    n, l = 16384, 136
+    rc, w64 = _ws(L, n, n, 128, 8, prec=rqr.FP64)
     assert rc == 0 and 0.15e9 < w64 < 0.25e9
-    rc, w64x = _ws(L, 16384, 16384, 128, 8, prec=2)
+    rc, w64x = _ws(L, n, n, 128, 8, prec=rqr.FP64X)
     assert rc == 0 and 1.2e9 < w64x < 1.4e9
-    rc, w32 = _ws(L, 16384, 16384, 128, 8, prec=1)
-    assert rc == 0 and abs(w32 - w64 / 2) <= 0.01 * w64
+    planes8 = 2 ** 30 + 8 * l * n   # op(B) chunk + op(A) planes of G
+    rc, w32 = _ws(L, n, n, 128, 8, prec=rqr.FP32)
+    assert rc == 0 and abs(w32 - w64 / 2 - planes8) <= 0.02 * w64
+    for prec, bpe in ((rqr.TF32, 4), (rqr.BF16X3, 4), (rqr.TF32X3, 8)):
+        rc, wm = _ws(L, n, n, 128, 8, prec=prec)
+        assert rc == 0 and abs(wm - w64 - min(2 ** 30, bpe * n * n) - bpe * l * n) <= 0.02 * w64, (prec, wm)
     assert _ws(L, 16384, 16384, 128, 8, sketch=1)[1] <= w64
     sizes = [_ws(L, n, n, 128, 8)[1] for n in (256, 1000, 4096, 8192, 16384)]
     assert sizes == sorted(sizes)

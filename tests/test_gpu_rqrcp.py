@@ -285,7 +285,7 @@ def test_wait_limit_timeout_then_recovery():
     ordinary work for a CTA that arrives before the others gives up: no kernel
     is altered, nothing faults. Then the default limit is restored and the same
     handle factors the same matrix correctly."""
-    m, n, b, p = 2048, 2048, 128, 8
+    m, n, b, p = 1024, 1024, 64, 8
     A = inputs.a_fast(n, seed=21, m=m)
     G = inputs.sketch_gaussian(22, b + p, m)
     try:

@@ -67,13 +67,19 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("m,n,b,p,q,fam", CASES)
-def test_rurv_parity(m, n, b, p, q, fam):
+# sizes that reach the split-K and large-tile paths of the products, and in
+# FP64X the column-chunked tensor-core kernel with transposed power products
+LARGE = [(1100, 1024, 128, 10, 1, "fast", "fp64"), (1100, 1024, 128, 10, 1, "fast", "fp64x"),
+         (1300, 1280, 128, 10, 2, "gauss", "fp64x"), (640, 600, 64, 16, 0, "s", "fp64x")]
+
+
+@pytest.mark.parametrize("m,n,b,p,q,fam,prec", [c + ("fp64",) for c in CASES] + LARGE)
+def test_rurv_parity(m, n, b, p, q, fam, prec):
     A = {"fast": inputs.a_fast, "gauss": inputs.a_gauss, "s": inputs.a_s}[fam](n, seed=m + b + q, m=m)
     G = inputs.resample_blocks(77 + q, m, n, b, p, full_last=True)
     F0, TU0, WV0, TV0, done0 = oracle.rurv(A, b, p, q, G)
     Ad = dev(A)
-    TU, WV, TV, info = rqr.rurv_factor(Ad, b, p, q, G=torch.from_numpy(G).cuda())
+    TU, WV, TV, info = rqr.rurv_factor(Ad, b, p, q, G=torch.from_numpy(G).cuda(), prec=prec)
     assert info == 0
     F, TU, WV, TV = host(Ad), host(TU), host(WV), host(TV)
     Q, P = factors(F, TU, WV, TV, b)
