@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
     ap.add_argument("--prec", default="fp64x", choices=["fp64", "fp64x"],
                     help="fp64: FP64 DMMA products; fp64x: FP64-accurate bf16 tensor-core products")
+    ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
+                    help="mixed-precision modes timed on the same workload (comma list, '' for none)")
+    ap.add_argument("--legs", default="c2,c4,cpu",
+                    help="further measurements: c2 (8192^2 FP64 vs FP32), c4 (URV 8192^2, q = 0, 1, 2), "
+                         "cpu (LAPACK dgeqp3 and the single-threaded oracle)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the native FP64 path")
     ap.add_argument("--no-verify", action="store_true", help="skip the accuracy probe (profiling runs)")
     ap.add_argument("--seed", type=int, default=1505)
@@ -160,6 +165,193 @@ def make_matrix(n, seed, device):
     return inputs.torch_svd_matrix(n, n, inputs.spectrum_exp(n, 800.0), seed, device=device)
 
 
+def norm2_est(A, iters=40):
+    """||A||_2 by power iteration on A^T A (probes only; about 1e-6 relative)."""
+    import torch
+
+    g = torch.Generator(device=A.device).manual_seed(11)
+    x = torch.randn(A.shape[1], 1, generator=g, device=A.device, dtype=torch.float64)
+    s = 0.0
+    for _ in range(iters):
+        y = A.double() @ x
+        x = A.double().T @ y
+        s = torch.linalg.norm(x).item()
+        x /= s
+    return s ** 0.5
+
+
+def probe_errors(A0, F, T, perm, b, nA2):
+    """Residual ||A P X - Q R X|| / (||A||_2 ||X||) and orthogonality
+    ||Q^T Q X - X|| / ||X|| on four random vectors (the CPU cannot form Q at
+    these sizes)."""
+    import torch
+
+    g = torch.Generator(device=F.device).manual_seed(7)
+    X = torch.randn(F.shape[1], 4, generator=g, device=F.device, dtype=torch.float64)
+    Fd = F.double()
+    Td = T.double()
+    R = torch.triu(Fd)
+    APx = A0.double()[:, perm.long()] @ X
+    res = (torch.linalg.norm(APx - apply_q(Fd, Td, b, R @ X)) / (nA2 * torch.linalg.norm(X))).item()
+    orth = (torch.linalg.norm(apply_q(Fd, Td, b, apply_q(Fd, Td, b, X), transpose=True) - X)
+            / torch.linalg.norm(X)).item()
+    return res, orth
+
+
+def timed_calls(fn, reset, steps, stream):
+    """One untimed call, then the mean CUDA-event time (ms) of `steps` calls."""
+    import torch
+
+    reset()
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def leg_c2(a, dev, stream):
+    """Config C2: m = n = 8192, b = 128, p = 8, N(0,1) plus a rank-200 spike
+    U diag(100 0.9^i) V^T; FP64 (DMMA products) against FP32 (3xTF32 tensor-core
+    products): time, residual, orthogonality, and the first block's pivots and R
+    rows against the oracle (same A, same G)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1505_08115_gb300 import inputs, rqr
+    from paper_1505_08115_gb300.flops import rqrcp_flops
+
+    n, b, p = 8192, 128, 8
+    A0 = inputs.torch_spike_matrix(n, seed=a.seed + 2, device=dev)
+    G = inputs.torch_sketch_gaussian(a.seed + 3, b + p, n, device=dev)
+    nA2 = norm2_est(A0)
+    fl = rqrcp_flops(n, n, b, p)["total"]
+    t0 = time.perf_counter()
+    F0, T0, perm0, done = oracle.rqrcp(np.asfortranarray(A0.cpu().numpy()), b, p,
+                                       np.asfortranarray(G.cpu().numpy()), max_blocks=1)
+    out = {"workload": f"rqrcp m=n={n} b={b} p={p} downdate, A = N(0,1) + U diag(100 0.9^i) V^T (rank 200)",
+           "oracle_first_block_s": time.perf_counter() - t0}
+    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        A = rqr.empty_colmajor(n, n, dt, dev)
+        Ain = A0.to(dt)
+        Gd = rqr.colmajor(G.to(dt))
+        T = rqr.empty_colmajor(b, n, dt, dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.PRECISIONS[prec]), dtype=torch.uint8, device=dev)
+
+        def call():
+            rqr.rqrcp_factor(A, b, p, G=Gd, T=T, perm=perm, work=work, check=False)
+
+        ms = timed_calls(call, lambda: A.copy_(Ain), 2, stream)
+        A.copy_(Ain)
+        _, _, info = rqr.rqrcp_factor(A, b, p, G=Gd, T=T, perm=perm, work=work)
+        res, orth = probe_errors(A0, A, T, perm, b, nA2)
+        pc = perm.cpu().numpy()
+        pos = np.empty(n, dtype=np.int64)
+        pos[pc] = np.arange(n)
+        Rg = torch.triu(A[:b, :].double()).cpu().numpy()[:, pos[perm0]]
+        out[prec] = {"ms": ms, "value": fl / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "device_status": info,
+                     "residual": res, "orthogonality": orth,
+                     "first_block_pivots_equal_oracle": bool(np.array_equal(pc[:b], perm0[:b])),
+                     "first_block_pivot_overlap": len(set(pc[:b]) & set(perm0[:b])) / b,
+                     "first_block_max_dR_over_norm2": float(np.abs(np.triu(Rg) - np.triu(F0[:b, :])).max() / nA2)}
+        del A, Ain, Gd, T, work
+    out["fp32_speedup_vs_fp64"] = out["fp64"]["ms"] / out["fp32"]["ms"]
+    return out
+
+
+def leg_c4(a, dev, stream):
+    """Config C4: orthonormal-pivot URV with diagonalised blocks (Method 3,
+    Fig. blockRRQR), m = n = 8192, b = 128, p = 10, q = 0, 1, 2, A with
+    singular values 1/(1+i)^2 plus 1e-8 N(0,1) noise; FP64X and TF32 products.
+    Reports GFLOP/s (URV flop model), |R_ii| / sigma_i (sigma from the FP64
+    SVD of A) and the off-diagonal mass ||R - diag R||_F / ||R||_F."""
+    import torch
+
+    from paper_1505_08115_gb300 import inputs, rqr
+    from paper_1505_08115_gb300.flops import rurv_flops
+
+    n, b, p = 8192, 128, 10
+    A0 = inputs.torch_svd_matrix(n, n, inputs.spectrum_invsq(n), a.seed + 4, device=dev)
+    g = torch.Generator(device=dev).manual_seed(a.seed + 5)
+    A0 = rqr.colmajor(A0 + 1e-8 * torch.randn(n, n, generator=g, device=dev, dtype=torch.float64))
+    t0 = time.perf_counter()
+    sv = torch.linalg.svdvals(A0)
+    torch.cuda.synchronize()
+    out = {"workload": f"rurv (diagonalised blocks) m=n={n} b={b} p={p}, A = U diag(1/(1+i)^2) V^T + 1e-8 N(0,1)",
+           "svd_s": time.perf_counter() - t0}
+    A = rqr.empty_colmajor(n, n, torch.float64, dev)
+    for prec in ("fp64x", "tf32"):
+        work = torch.empty(rqr.workspace_bytes(n, n, b, p, 2, rqr.PRECISIONS[prec]), dtype=torch.uint8, device=dev)
+        for q in (0, 1, 2):
+            def call():
+                rqr.rurv_factor(A, b, p, q, seed=a.seed + 6, work=work, check=False, diag=True, prec=prec)
+
+            ms = timed_calls(call, lambda: A.copy_(A0), 1, stream)
+            A.copy_(A0)
+            *_, info = rqr.rurv_factor(A, b, p, q, seed=a.seed + 6, work=work, diag=True, prec=prec)
+            R = torch.triu(A)
+            d = torch.diagonal(R).abs()
+            ratio = d / sv
+            k = n // 8
+            out[f"{prec}_q{q}"] = {
+                "ms": ms, "value": rurv_flops(n, n, b, p, q, diag=True)["total"] / (ms / 1e3) / 1e9,
+                "unit": "GFLOP/s", "device_status": info,
+                "Rii_over_sigma_first_n/8": {"min": ratio[:k].min().item(), "median": ratio[:k].median().item(),
+                                             "max": ratio[:k].max().item()},
+                "Rii_over_sigma_all": {"min": ratio.min().item(), "median": ratio.median().item(),
+                                       "max": ratio.max().item()},
+                "offdiag_mass": (torch.linalg.norm(R - torch.diag(torch.diagonal(R))) / torch.linalg.norm(R)).item()}
+        del work
+    return out
+
+
+def leg_cpu(a):
+    """Classical CPU context: LAPACK dgeqp3 (scipy, all host cores) on a 4096^2
+    matrix of the exp(-i/800) family, and the oracle on config C1 (1000^2,
+    b = 64, p = 10) with all cores and single-threaded."""
+    import json as _json
+    import numpy as np
+    import scipy.linalg
+
+    from paper_1505_08115_gb300 import inputs
+    from paper_1505_08115_gb300.flops import conventional_qr_flops
+
+    nl = 4096
+    A = inputs.svd_matrix(a.seed + 7, nl, nl, inputs.spectrum_exp(nl, 800.0))
+    t0 = time.perf_counter()
+    scipy.linalg.qr(A, pivoting=True, mode="r", overwrite_a=True, check_finite=False)
+    dt = time.perf_counter() - t0
+    out = {"lapack_dgeqp3": {"n": nl, "s": dt, "gflops_conventional": conventional_qr_flops(nl, nl) / dt / 1e9,
+                             "cores": len(os.sched_getaffinity(0))}}
+    code = ("import sys, time, json; sys.path.insert(0, %r)\n"
+            "import oracle\nfrom paper_1505_08115_gb300 import inputs\n"
+            "from paper_1505_08115_gb300.flops import rqrcp_flops\n"
+            "A = inputs.decade_matrix(1000, seed=1505); G = inputs.sketch_gaussian(1506, 74, 1000)\n"
+            "oracle.rqrcp(A[:200, :200], 64, 10, G[:, :200])\n"
+            "t = time.perf_counter(); oracle.rqrcp(A, 64, 10, G); t = time.perf_counter() - t\n"
+            "print(json.dumps({'s': t, 'gflops': rqrcp_flops(1000, 1000, 64, 10)['total'] / t / 1e9}))\n") % ROOT
+    for label, threads in (("oracle_c1_all_cores", None), ("oracle_c1_1_thread", "1")):
+        env = dict(os.environ)
+        if threads:
+            env["OMP_NUM_THREADS"] = threads
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        try:
+            out[label] = _json.loads(r.stdout.strip().splitlines()[-1])
+            out[label]["threads"] = int(threads) if threads else len(os.sched_getaffinity(0))
+        except (ValueError, IndexError):
+            out[label] = {"error": (r.stderr or r.stdout)[-300:]}
+    return out
+
+
 def workload_config(a):
     return {"workload": f"rqrcp m=n={a.n} b={a.b} p={a.p} sketch={a.sketch}, A = U diag(exp(-i/800)) V^T",
             "m": a.n, "n": a.n, "b": a.b, "p": a.p, "sketch": a.sketch, "precision": a.prec,
@@ -229,9 +421,11 @@ def run_reference(a, rank):
     ms = 1e3 * sum(times) / len(times)
     val = fl / (ms / 1e3) / 1e9
     cores = len(os.sched_getaffinity(0))
+    cfg = workload_config(a)
+    cfg["precision"] = "fp64: the CPU oracle (plain FP64 loops, OpenMP over independent columns)"
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                             "sample": f"first {blocks} block of the {a.n}x{a.n} factorization per step"},
            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -272,27 +466,29 @@ def main():
     A = rqr.empty_colmajor(n, n, torch.float64, dev)
     T = rqr.empty_colmajor(b, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    work = torch.empty(rqr.workspace_bytes(n, n, b, p, -1, rqr.FP64X, sk), dtype=torch.uint8, device=dev)
+    modes = [x for x in a.modes.split(",") if x]
+    work = torch.empty(max(rqr.workspace_bytes(n, n, b, p, -1, rqr.PRECISIONS[x], sk) for x in ["fp64x"] + modes),
+                       dtype=torch.uint8, device=dev)
     seed = a.seed + 1 + rank
     stream = torch.cuda.current_stream(dev)
     fl = rqrcp_flops(n, n, b, p, resample=(sk == rqr.SKETCH_RESAMPLE))
 
     def measure(prec):
         """W untimed + K timed factorizations in one precision mode."""
-        emu = prec == "fp64x"
 
         def step():
-            rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False, emulated=emu)
+            rqr.rqrcp_factor(A, b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work, check=False, prec=prec)
 
         for _ in range(a.warmup):
             A.copy_(A0)
             step()
         torch.cuda.synchronize()
-        res = orth = info = None
+        res = orth = info = perm_out = None
         if not a.no_verify:
             # accuracy of one factorization (random probes; the CPU cannot form Q at this size)
             _, _, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work,
-                                          emulated=emu)
+                                          prec=prec)
+            perm_out = perm.clone()
             g = torch.Generator(device=dev).manual_seed(7)
             X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
             R = torch.triu(A)
@@ -324,7 +520,7 @@ def main():
         rqr.profile_enable(False)
         ms = slowest_rank_ms(sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps, dist, dev)
         return {"ms": ms, "prof": prof, "kern": kern, "residual": res, "orthogonality": orth, "info": info,
-                "clocks": ck, "step": step}
+                "clocks": ck, "step": step, "perm": perm_out}
 
     head = measure(a.prec)
     ms, prof = head["ms"], head["prof"]
@@ -380,6 +576,36 @@ def main():
                            "update_tflops": base["prof"]["update"]["flops"] / (base["prof"]["update"]["ms"] / 1e3)
                            / 1e12 if base["prof"]["update"]["ms"] else None, "clocks": base["clocks"]}
         out["speedup_vs_fp64_gpu"] = base["ms"] / ms
+    fp64_ms = out.get("fp64_gpu", {}).get("ms_per_step")
+
+    if modes:
+        # the mixed-precision modes on the same workload: speed-up over the
+        # native FP64 GPU path at each mode's measured accuracy
+        out["mixed"] = {}
+        ref_perm = head["perm"]
+        for mode in modes:
+            r = measure(mode)
+            kern = r["kern"]
+            kms = kern["ms"] if kern["ms"] > 0 else float("nan")
+            ent = {"ms_per_step": r["ms"], "value": job_gflops(fl["total"], world, r["ms"]), "unit": "GFLOP/s",
+                   "residual": r["residual"], "orthogonality": r["orthogonality"], "device_status": r["info"],
+                   "speedup_vs_fp64_gpu": (fp64_ms / r["ms"]) if fp64_ms else None,
+                   "speedup_vs_fp64x": ms / r["ms"],
+                   "phases_ms": {k: v["ms"] / a.steps for k, v in r["prof"].items()},
+                   "product_kernel": {"name": "k_tcmix (tcgen05.mma, FP32 accumulation in TMEM)",
+                                      "launches_per_step": kern["launches"] // a.steps,
+                                      "ms_per_step": kern["ms"] / a.steps,
+                                      "hbm_gbs": kern["bytes"] / (kms / 1e3) / 1e9,
+                                      "hbm_frac": kern["bytes"] / (kms / 1e3) / 1e9 / pk["hbm_gbs"],
+                                      "tensor_tflops": kern["flops"] / (kms / 1e3) / 1e12,
+                                      "peak_source": f"{src} HBM {pk['hbm_gbs']} GB/s"}}
+            if ref_perm is not None and r["perm"] is not None:
+                # pivots are reported, not asserted: set overlap with the FP64X run's
+                # (which matches the oracle's on the parity tests)
+                pa_, pb_ = r["perm"].cpu().numpy(), ref_perm.cpu().numpy()
+                ent["pivot_overlap_vs_fp64x"] = {str(k): len(set(pa_[:k]) & set(pb_[:k])) / k
+                                                 for k in (b, 8 * b, n // 2)}
+            out["mixed"][mode] = ent
 
     if not a.no_e2e:
         # end to end through the same C-ABI call with host buffers: pinned H2D of A,

@@ -235,10 +235,13 @@ int rqr_profile_enable(rqr_handle_t h, int on);
 int rqr_profile_read(rqr_handle_t h, double* ms, double* flops, int64_t* launches, int nphase);
 
 /* Waits for the handle's stream, then writes the summed CUDA-event time (ms),
- * the algorithmic tensor-core flops (36 bf16 digit-pair products of 2 M N K
- * each), the algorithmic DRAM bytes (both operands' digit planes once, C read
- * and written) and the launch count of the tcgen05 FP64X product kernel
- * launched while tracing was on (host outputs, any may be NULL); clears them. */
+ * the algorithmic tensor-core flops, the algorithmic DRAM bytes and the launch
+ * count of the tcgen05 product kernels launched while tracing was on (host
+ * outputs, any may be NULL); clears them. FP64X kernel: 36 bf16 digit-pair
+ * products of 2 M N K flops each, bytes = both operands' 8 digit planes (16
+ * bytes per element) once plus C read and written. Mixed-mode kernel: 1
+ * (TF32) or 3 (3XBF16, 3XTF32) products of 2 M N K, bytes = both operands'
+ * planes (4 or 8 bytes per element) once plus C read and written. */
 int rqr_profile_kernel_read(rqr_handle_t h, double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* Library version string (static storage). */

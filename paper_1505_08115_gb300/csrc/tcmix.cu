@@ -446,7 +446,17 @@ bool mix_tc_impl(const Ctx& c, bool ta, bool tb, int M, int N, int K, IT alpha, 
     a.part = part;
     a.status = c.status;
     const int grid = std::min(mn * a.S, c.sms);
+    const bool timed = c.kt && c.kt->start(c.stream);
     k_tcmix<MODE, IT><<<grid, MX_THREADS, mix_smem<MODE>(), c.stream>>>(mapA, nn == nc ? mapB : mapBlast, a);
+    if (timed) {
+      // flops: the 1 or 3 operand-plane products, 2 M N K each; bytes: both
+      // operands' planes read once, C read (beta != 0) and written, or the
+      // split-K partials written
+      const double planes = (double)MX::NP * MX::ESZ * ((double)M + nn) * K;
+      const double cbytes = a.S > 1 ? (double)sizeof(IT) * a.S * M * nn
+                                    : (double)sizeof(IT) * M * nn * (beta != IT(0) ? 2.0 : 1.0);
+      c.kt->stop(c.stream, (MX::NP == 2 ? 3.0 : 1.0) * 2.0 * (double)M * nn * K, planes + cbytes);
+    }
     note_launch(c);
     if (a.S > 1) {
       const size_t MN = (size_t)M * nn;

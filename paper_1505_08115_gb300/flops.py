@@ -13,6 +13,14 @@ are C_mm = 2 and the Householder counts:
     + 2 m' n'^2 - 2 n'^3 / 3                      (last block, classical QRCP)
 with m' = m - k0, n' = n - k0 and l = b + p. The conventional rate of a QR,
 (2 m n^2 - 2 n^3 / 3) / t, is reported beside it.
+
+The orthonormal-pivot (URV) method counts, per block of b_i columns,
+  (2 q + 1) 2 l m' n'                             (sketch and power products)
+  + 2 n' l^2                                      (QR of the n' x l sketch)
+  + 4 m n' b_i                                    (right apply, all m rows)
+  + 2 m' b_i^2 - 2 b_i^3 / 3 + 4 m' (n' - b_i) b_i (panel QR, trailing update)
+  [+ 6 b_i^3 + 2 (k0 + n' - b_i) b_i^2           (diagonalised block, Sec. 6.2)]
+and stops once k0 >= k for a truncated rank-k factorization.
 """
 from __future__ import annotations
 
@@ -50,3 +58,24 @@ def rqrcp_flops(m: int, n: int, b: int, p: int, resample: bool = False, max_bloc
 
 def conventional_qr_flops(m: int, n: int) -> float:
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def rurv_flops(m: int, n: int, b: int, p: int, q: int, k: int = 0, diag: bool = False) -> dict:
+    l = b + p
+    ph = {"sketch": 0.0, "pivot": 0.0, "right": 0.0, "panel": 0.0, "update": 0.0}
+    k0 = 0
+    while k0 < n:
+        mp, np_ = m - k0, n - k0
+        bi = min(b, np_)
+        ph["sketch"] += (2 * q + 1) * 2.0 * l * mp * np_
+        ph["pivot"] += 2.0 * np_ * l * l
+        ph["right"] += 4.0 * m * np_ * bi
+        ph["panel"] += 2.0 * mp * bi * bi - 2.0 * bi ** 3 / 3.0
+        ph["update"] += 4.0 * mp * (np_ - bi) * bi
+        if diag:
+            ph["panel"] += 6.0 * bi ** 3 + 2.0 * (k0 + np_ - bi) * bi * bi
+        k0 += bi
+        if 0 < k <= k0:
+            break
+    ph["total"] = sum(ph.values())
+    return ph

@@ -53,3 +53,18 @@ def test_sketch_modes():
     for key in ("pivot", "panel", "update", "final"):
         assert down[key] == res[key]
     assert res["sketch"] > down["sketch"] + down["downdate"]
+
+
+def test_rurv_flops_terms():
+    """q = 0, p = 0, one block: sketch 2 b m n, QR of Z 2 n b^2, right apply
+    4 m n b, panel Householder, no update; the power steps add 4 l m' n' per q;
+    truncation stops after the block that reaches k."""
+    from paper_1505_08115_gb300.flops import rurv_flops
+    m, n, b = 100, 40, 40
+    f = rurv_flops(m, n, b, 0, 0)
+    assert f["sketch"] == 2 * b * m * n and f["right"] == 4 * m * n * b and f["update"] == 0
+    assert f["panel"] == 2 * m * b * b - 2 * b ** 3 / 3 and f["pivot"] == 2 * n * b * b
+    f2 = rurv_flops(m, n, b, 0, 2)
+    assert f2["sketch"] == 5 * f["sketch"]
+    full, trunc = rurv_flops(500, 400, 64, 8, 1), rurv_flops(500, 400, 64, 8, 1, k=100)
+    assert trunc["total"] < full["total"] and trunc["update"] == 4 * 500 * 336 * 64 + 4 * 436 * 272 * 64

@@ -121,13 +121,20 @@ def test_mixed_chunked_long_k(mode):
 
 
 def test_mixed_3x_modes_beat_tf32():
-    """The split modes recover accuracy: on the same product the 3xBF16 error
-    is at least 30x and the 3xTF32 error at least 300x below TF32's."""
+    """The split modes recover accuracy: on the same product (K = 2048) the
+    3xBF16 and 3xTF32 errors are at least 30x below TF32's. Both then sit at
+    the FP32 accumulation floor (measured 54x and 78x on GB300), so the 3xTF32
+    operands' extra 6 bits show only where K is short: at K = 64 its error is
+    at least 4x below 3xBF16's (measured 7x)."""
     r = np.random.default_rng(3)
     A, B = r.standard_normal((512, 2048)), r.standard_normal((2048, 512))
     ref = A @ B
     err = {m: np.abs(host(rqr.gemm(dev(A), dev(B), prec=m)) - ref).max() for m in MODES}
-    assert err["3xbf16"] * 30 <= err["tf32"] and err["3xtf32"] * 300 <= err["tf32"], err
+    assert err["3xbf16"] * 30 <= err["tf32"] and err["3xtf32"] * 30 <= err["tf32"], err
+    A, B = r.standard_normal((512, 64)), r.standard_normal((64, 512))
+    ref = A @ B
+    e16, e32 = (np.abs(host(rqr.gemm(dev(A), dev(B), prec=m)) - ref).max() for m in ("3xbf16", "3xtf32"))
+    assert e32 * 4 <= e16, (e16, e32)
 
 
 def _factor_check(A, b, p, G, mode, prec):
