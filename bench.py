@@ -472,6 +472,7 @@ def main():
     seed = a.seed + 1 + rank
     stream = torch.cuda.current_stream(dev)
     fl = rqrcp_flops(n, n, b, p, resample=(sk == rqr.SKETCH_RESAMPLE))
+    nA2 = norm2_est(A0) if not a.no_verify else None
 
     def measure(prec):
         """W untimed + K timed factorizations in one precision mode."""
@@ -489,14 +490,7 @@ def main():
             _, _, info = rqr.rqrcp_factor(A.copy_(A0), b, p, seed=seed, sketch=sk, T=T, perm=perm, work=work,
                                           prec=prec)
             perm_out = perm.clone()
-            g = torch.Generator(device=dev).manual_seed(7)
-            X = torch.randn(n, 4, generator=g, device=dev, dtype=torch.float64)
-            R = torch.triu(A)
-            APx = A0[:, perm.long()] @ X
-            res = (torch.linalg.norm(APx - apply_q(A, T, b, R @ X)) / torch.linalg.norm(APx)).item()
-            orth = (torch.linalg.norm(apply_q(A, T, b, apply_q(A, T, b, X), transpose=True) - X)
-                    / torch.linalg.norm(X)).item()
-            del R, APx
+            res, orth = probe_errors(A0, A, T, perm, b, nA2)
         clocks = Clocks(device_index_for_smi(local_rank))
         if dist:
             dist.barrier()
@@ -563,6 +557,8 @@ def main():
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "effective_gflops": job_gflops(conventional_qr_flops(n, n), world, ms),
            "residual": head["residual"], "orthogonality": head["orthogonality"], "device_status": head["info"],
+           "accuracy_probe": "residual ||A P X - Q R X|| / (||A||_2 ||X||), orthogonality ||Q^T Q X - X|| / ||X||, "
+                             "X: 4 random vectors; ||A||_2 by power iteration",
            "phases": {k: {"ms": v["ms"] / a.steps, "gflops": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0,
                           "launches": v["launches"] // a.steps} for k, v in prof.items()},
            "roofline": roof, "gpu_launches": launches, "clocks": head["clocks"]}
@@ -633,6 +629,19 @@ def main():
         out["e2e"] = {"value": job_gflops(fl["total"], world, em), "unit": "GFLOP/s",
                       "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n + 8 * b * n + 4 * n}
         del Ah, Fh
+
+    legs = [x for x in a.legs.split(",") if x]
+    if rank == 0 and legs:
+        # further configurations (rank 0 only; the other ranks wait at the final barrier)
+        out["legs"] = {}
+        del A, T, work
+        torch.cuda.empty_cache()
+        if "c2" in legs:
+            out["legs"]["c2"] = leg_c2(a, dev, stream)
+        if "c4" in legs:
+            out["legs"]["c4"] = leg_c4(a, dev, stream)
+        if "cpu" in legs:
+            out["legs"]["cpu"] = leg_cpu(a)
 
     if rank == 0 and not a.no_cpu_baseline:
         from paper_1505_08115_gb300 import inputs

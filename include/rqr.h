@@ -200,6 +200,40 @@ int rqr_gemm(rqr_handle_t h, int prec, int ta, int tb, int M, int N, int K, doub
              const void* B, int ldb, double beta, void* C, int ldc, void* work, size_t lwork);
 int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes);
 
+/* Differentiable form (no counterpart in the paper): reverse-mode derivative
+ * of the truncated factorization X = A P = [Q1 Q2] [R11 R12; 0 R22] with the
+ * column transformation P held fixed (the pivots of rqrcp_factor, or the
+ * orthonormal P of rurv_factor), outputs Q1 (m x k) and R1 = [R11 R12]
+ * (k x n), 1 <= k <= n <= m, FP64 data. Given the cotangents Qbar (m x k) and
+ * Rbar (k x n; only the upper triangle of its leading k x k block is read),
+ *   X2bar = Q1 R12bar,  Q1bar' = Qbar + X2 R12bar^T,
+ *   M = R11 R11bar^T - Q1bar'^T Q1,
+ *   X1bar = (Q1bar' + Q1 (tril(M) + tril(M, -1)^T)) R11^-T
+ * (the thin-QR adjoint applied to the leading block, plus the product rule
+ * for R12 = Q1^T X2).
+ *   Q        (device) Q1, m x k, ld ldq (e.g. from rqr_form_q with ncols = k).
+ *   F        (device) the factored matrix of the factor call: R11, R12 in the
+ *            upper triangle of its first k rows, ld ldf.
+ *   perm     (device, optional) the pivots of rqrcp_factor: then X2 is
+ *            gathered from A (device, m x n, ld lda, read only when k < n) and
+ *            Abar(:, perm[j]) = Xbar(:, j), so Abar is the cotangent of A.
+ *            NULL: X2 (device, m x (n - k), ld ldx2, = A P(:, k:n), read only
+ *            when k < n) is given, and Abar receives Xbar, the cotangent of
+ *            X = A P (the caller applies P^T).
+ *   Abar     (device, out) m x n, ld ldab.
+ *   work     (device) rqr_qr_adjoint_workspace_bytes bytes.
+ * A zero diagonal entry of R11 (rank-deficient leading block) gives
+ * RQR_ERR_NONFINITE in *info; the rows it touches are left unsolved. */
+int rqr_qr_adjoint(rqr_handle_t h, int m, int n, int k, const void* Q, int ldq, const void* F, int ldf,
+                   const void* A, int lda, const int32_t* perm, const void* X2, int ldx2, const void* Qbar,
+                   int ldqb, const void* Rbar, int ldrb, void* Abar, int ldab, void* work, size_t lwork,
+                   int* info);
+int rqr_qr_adjoint_workspace_bytes(int m, int n, int k, size_t* bytes);
+
+/* R (device, out, k x n, ld ldr) = upper triangle of the first k rows of the
+ * factored matrix F (device, ld ldf), zeros below; FP64. */
+int rqr_copy_r(rqr_handle_t h, int k, int n, const void* F, int ldf, void* R, int ldr);
+
 /* Fills out[0:count] (device) with N(0,1) samples: element e is lane e%4 of
  * Philox4x32-10 block e/4 with counter {lo(e/4), hi(e/4), lo(stream),
  * hi(stream)} and key {lo(seed), hi(seed)}, through Box-Muller on the pairs

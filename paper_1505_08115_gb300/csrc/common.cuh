@@ -253,6 +253,15 @@ void r_transpose(const Ctx& c, int kk, int cols, const T* F, int ldf, T* M, int 
 template <typename T>
 void copy_lower(const Ctx& c, int r, int cols, const T* src, int lds, T* dst, int ldd);
 
+// Differentiable form (adjoint.cu): the reverse-mode derivative of
+// X = A P = Q R, truncated to k columns of Q, with P fixed.
+size_t qr_adjoint_work_elems(int m, int n, int k, int sms);
+int qr_adjoint(const Ctx& c, int m, int n, int k, const double* Q1, int ldq, const double* F, int ldf, const double* A,
+               int lda, const int32_t* perm, const double* X2, int ldx2, const double* Qb, int ldqb, const double* Rb,
+               int ldrb, double* Ab, int ldab, double* work);
+// R (k x n) = upper triangle of the first k rows of F, zeros below.
+void copy_upper(const Ctx& c, int k, int n, const double* F, int ldf, double* R, int ldr);
+
 // Context of a live handle (false for a NULL or destroyed handle).
 bool handle_ctx(rqr_handle_t h, Ctx* out);
 

@@ -947,6 +947,66 @@ int rqr_gemm_workspace_bytes(int prec, int M, int N, int K, size_t* bytes) {
   return RQR_OK;
 }
 
+int rqr_qr_adjoint_workspace_bytes(int m, int n, int k, size_t* bytes) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (k < 0 || k > n) return -3;
+  if (!bytes) return -4;
+  int dev = 0, sms = rqr::kNumSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  *bytes = sizeof(double) * rqr::qr_adjoint_work_elems(m, n, k, sms) + 256;
+  return RQR_OK;
+}
+
+int rqr_qr_adjoint(rqr_handle_t h, int m, int n, int k, const void* Q, int ldq, const void* F, int ldf, const void* A,
+                   int lda, const int32_t* perm, const void* X2, int ldx2, const void* Qbar, int ldqb, const void* Rbar,
+                   int ldrb, void* Abar, int ldab, void* work, size_t lwork, int* info) {
+  if (!valid(h)) return -1;
+  if (m < 0) return -2;
+  if (n < 1 || n > m) return -3;
+  if (k < 1 || k > n) return -4;
+  if (!Q) return -5;
+  if (ldq < std::max(1, m)) return -6;
+  if (!F) return -7;
+  if (ldf < std::max(1, m)) return -8;
+  if (perm && k < n && !A) return -9;
+  if (perm && k < n && lda < std::max(1, m)) return -10;
+  if (!perm && k < n && !X2) return -12;
+  if (!perm && k < n && ldx2 < std::max(1, m)) return -13;
+  if (!Qbar) return -14;
+  if (ldqb < std::max(1, m)) return -15;
+  if (!Rbar) return -16;
+  if (ldrb < k) return -17;
+  if (!Abar) return -18;
+  if (ldab < std::max(1, m)) return -19;
+  if (!work) return -20;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -20;
+  if (lwork < sizeof(double) * rqr::qr_adjoint_work_elems(m, n, k, h->sms)) return RQR_ERR_WORKSPACE;
+  cudaGetLastError();
+  rqr::Ctx c = make_ctx(h);
+  cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
+  rqr::qr_adjoint(c, m, n, k, static_cast<const double*>(Q), ldq, static_cast<const double*>(F), ldf,
+                  static_cast<const double*>(A), lda, perm, static_cast<const double*>(X2), ldx2,
+                  static_cast<const double*>(Qbar), ldqb, static_cast<const double*>(Rbar), ldrb,
+                  static_cast<double*>(Abar), ldab, static_cast<double*>(work));
+  return finish(h, info);
+}
+
+int rqr_copy_r(rqr_handle_t h, int k, int n, const void* F, int ldf, void* R, int ldr) {
+  if (!valid(h)) return -1;
+  if (k < 0) return -2;
+  if (n < 0) return -3;
+  if (!F && k > 0 && n > 0) return -4;
+  if (ldf < std::max(1, k)) return -5;
+  if (!R && k > 0 && n > 0) return -6;
+  if (ldr < std::max(1, k)) return -7;
+  cudaGetLastError();
+  rqr::Ctx c = make_ctx(h);
+  rqr::copy_upper(c, k, n, static_cast<const double*>(F), ldf, static_cast<double*>(R), ldr);
+  return finish(h, nullptr);
+}
+
 const char* rqr_version(void) { return "rqr-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -98,23 +98,59 @@ __device__ __forceinline__ uint32_t tf32_rn(float f) {
   return u & 0xffffe000u;
 }
 
+// An FP64 value as two FP32 values, x = hi + lo + d with |d| <= 2^-47 |x|:
+// hi = the leading 24 significand bits (truncated), lo = the next 24 of the
+// remaining 29, both from the bit pattern with integer operations (GB300
+// runs FP64 arithmetic and conversions on its narrow FP64 pipe, which would
+// bound the splitting). Values outside FP32's normal range give hi = +-0 (below
+// 2^-126) or +-inf (at or above 2^128).
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(bits >> 32) & 0x80000000u;
+  const int e = (int)((bits >> 52) & 0x7ff) - 1023;  // x = 1.f 2^e
+  hi = lo = __uint_as_float(sign);
+  if (e < -126) return;
+  if (e > 127) {
+    hi = __uint_as_float(sign | 0x7f800000u);
+    return;
+  }
+  const unsigned long long f = bits & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
+  hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(f >> 29));
+  const uint32_t rem = (uint32_t)(f & 0x1FFFFFFFu);  // value rem 2^(e - 52)
+  if (rem == 0) return;
+  const int msb = 31 - __clz(rem);                   // rem in [2^msb, 2^(msb+1))
+  const int ef = e - 52 + msb + 127;
+  if (ef <= 0) return;
+  const uint32_t frac = msb >= 23 ? rem >> (msb - 23) : rem << (23 - msb);
+  lo = __uint_as_float(sign | ((uint32_t)ef << 23) | (frac & 0x7FFFFFu));
+}
+
 // The planes of one value: x ~ sum_p plane_p (MODE's split), written at
-// element `off` of each plane (planes pstride elements apart).
+// element `off` of each plane (planes pstride elements apart). FP32 and
+// integer operations only.
 template <int MODE, typename IT>
 __device__ __forceinline__ void put_planes(void* planes, size_t pstride, size_t off, IT x) {
+  float hi, lo;
+  if constexpr (sizeof(IT) == 8) {
+    split_f64(x, hi, lo);
+  } else {
+    hi = x;
+    lo = 0.f;
+  }
   if constexpr (MODE == RQR_3XBF16) {
     uint16_t* P = static_cast<uint16_t*>(planes);
-    const __nv_bfloat16 hi = __double2bfloat16((double)x);
-    const __nv_bfloat16 lo = __double2bfloat16((double)x - (double)__bfloat162float(hi));
-    P[off] = __bfloat16_as_ushort(hi);
-    P[pstride + off] = __bfloat16_as_ushort(lo);
+    const __nv_bfloat16 h16 = __float2bfloat16_rn(hi);
+    // hi - h16 is exact in FP32 (h16 is hi rounded to fewer bits)
+    const __nv_bfloat16 l16 = __float2bfloat16_rn((hi - __bfloat162float(h16)) + lo);
+    P[off] = __bfloat16_as_ushort(h16);
+    P[pstride + off] = __bfloat16_as_ushort(l16);
   } else {
     uint32_t* P = static_cast<uint32_t*>(planes);
-    const uint32_t big = tf32_rn((float)x);
+    const uint32_t big = tf32_rn(hi);
     P[off] = big;
     if constexpr (MODE == RQR_3XTF32) {
-      // x - big is exact in the input precision (big is x rounded to fewer bits)
-      P[pstride + off] = tf32_rn((float)(x - (IT)__uint_as_float(big)));
+      // hi - big is exact in FP32 (big is hi rounded to fewer bits)
+      P[pstride + off] = tf32_rn((hi - __uint_as_float(big)) + lo);
     }
   }
 }
@@ -302,16 +338,22 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
                      : a.beta == CT(1) ? (a.alpha == CT(1) ? 3 : a.alpha == CT(-1) ? 4 : 6)
                                        : 6;
     uint32_t tl = 0;
+    const bool needc = mode == 3 || mode == 4 || mode == 6;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       int m0, n0, kb, ke;
       tile_of(t, m0, n0, kb, ke);
       const int bf = tl & 1;
+      const int i = m0 + row;
+      if (needc && i < a.M) {
+        // pull this thread's C entries into L2 while the tile's MMAs run
+        const int jb = n0 + cg * MX_EPI_COLS, je = min(a.N, jb + MX_EPI_COLS);
+        for (int j = jb; j < je; ++j)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.C + i + (size_t)j * a.ldc));
+      }
       const bool got = mbar_wait(tfull(bf), (tl >> 1) & 1, abort, a.status);
       if (!__all_sync(0xffffffffu, got)) break;
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + bf * MX_BN + cg * MX_EPI_COLS;
-      const int i = m0 + row;
-      const bool needc = mode == 3 || mode == 4 || mode == 6;
       // 16 columns at a time: the buffer stays ours until the whole tile is
       // written (the MMA warp needs it again only two tiles later)
 #pragma unroll 1

@@ -32,7 +32,8 @@ FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 # every symbol declared in include/rqr.h
 EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_set_wait_limit_ns", "rqr_workspace_bytes",
            "rqrcp_factor", "rurv_factor",
-           "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_gauss_fill",
+           "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_qr_adjoint",
+           "rqr_qr_adjoint_workspace_bytes", "rqr_copy_r", "rqr_gauss_fill",
            "rqr_philox_raw",
            "rqr_profile_enable", "rqr_profile_read", "rqr_profile_kernel_read", "rqr_version")
 PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final", "right")
@@ -70,6 +71,9 @@ def load(path: str = SO_PATH):
         L.rqr_form_q_noalloc.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, i, i]
         L.rqr_gemm.argtypes = [vp, i, i, i, i, i, i, ctypes.c_double, vp, i, vp, i, ctypes.c_double, vp, i, vp, sz]
         L.rqr_gemm_workspace_bytes.argtypes = [i, i, i, i, ctypes.POINTER(sz)]
+        L.rqr_qr_adjoint.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, vp, vp, i, vp, i, vp, i, vp, i, vp, sz, ip]
+        L.rqr_qr_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(sz)]
+        L.rqr_copy_r.argtypes = [vp, i, i, vp, i, vp, i]
         L.rqr_gauss_fill.argtypes = [vp, u64, u64, i64, vp, i]
         L.rqr_philox_raw.argtypes = [vp, u32, u32, u32, u32, u32, i64, vp]
         L.rqr_profile_enable.argtypes = [vp, i]
@@ -271,6 +275,44 @@ def gemm(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, ta: bo
     if rc != 0:
         raise RQRError(f"rqr_gemm failed ({rc})")
     return C
+
+
+def copy_r(F: torch.Tensor, k: int) -> torch.Tensor:
+    """R (k x n, column-major) = upper triangle of the first k rows of the
+    factored FP64 matrix F."""
+    _require_cuda(F)
+    n = F.shape[1]
+    R = empty_colmajor(k, n, torch.float64, F.device)
+    rc = load().rqr_copy_r(handle(F.device), k, n, _ptr(F), _ld(F), _ptr(R), _ld(R) if n else max(1, k))
+    if rc != 0:
+        raise RQRError(f"rqr_copy_r failed ({rc})")
+    return R
+
+
+def qr_adjoint(Q1: torch.Tensor, F: torch.Tensor, Qbar: torch.Tensor, Rbar: torch.Tensor,
+               A: torch.Tensor | None = None, perm: torch.Tensor | None = None,
+               X2: torch.Tensor | None = None) -> torch.Tensor:
+    """Cotangent of A (with perm: Method-1 pivots) or of X = A P (with X2 =
+    A P(:, k:)) for the truncated factorization outputs Q1 (m x k) and
+    R1 (k x n) held in F; P fixed. All column-major FP64 on the GPU."""
+    _require_cuda(F)
+    m, k = Q1.shape
+    n = F.shape[1]
+    Abar = empty_colmajor(m, n, torch.float64, F.device)
+    sz = ctypes.c_size_t()
+    load().rqr_qr_adjoint_workspace_bytes(m, n, k, ctypes.byref(sz))
+    work = torch.empty(sz.value, dtype=torch.uint8, device=F.device)
+    info = ctypes.c_int(0)
+    rc = load().rqr_qr_adjoint(handle(F.device), m, n, k, _ptr(Q1), _ld(Q1), _ptr(F), _ld(F), _ptr(A),
+                               _ld(A) if A is not None else max(1, m), _ptr(perm), _ptr(X2),
+                               _ld(X2) if X2 is not None and X2.shape[1] > 0 else max(1, m), _ptr(Qbar), _ld(Qbar),
+                               _ptr(Rbar), _ld(Rbar), _ptr(Abar), _ld(Abar), _ptr(work), work.numel(),
+                               ctypes.byref(info))
+    if rc < 0:
+        raise RQRError(f"rqr_qr_adjoint: argument {-rc} invalid")
+    if rc > 0 or info.value:
+        raise RQRError(f"rqr_qr_adjoint: {STATUS.get(rc or info.value, rc or info.value)}")
+    return Abar
 
 
 def gauss_fill(seed: int, stream: int, count: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
