@@ -234,6 +234,42 @@ int rqr_qr_adjoint_workspace_bytes(int m, int n, int k, size_t* bytes);
  * factored matrix F (device, ld ldf), zeros below; FP64. */
 int rqr_copy_r(rqr_handle_t h, int k, int n, const void* F, int ldf, void* R, int ldr);
 
+/* Batched form (config C5; the paper factors one matrix at a time): many
+ * small FP32 matrices of different shapes factored in ONE persistent launch.
+ * Each CTA takes the next matrix from a queue (one atomic) and runs every step
+ * of the method for it. method:
+ *   RQR_BATCH_QRCP  randomized QRCP, Method 1 with over-sampling p and a fresh
+ *                   Gaussian per block (RESAMPLE layout), as rqrcp_factor;
+ *   RQR_BATCH_URV   orthonormal pivots with q power steps (Method 2), no
+ *                   over-sampling (p must be 0), truncated once k columns
+ *                   are done (k <= 0: all); in the last block the Householder
+ *                   QR of the power sketch's first b_i columns gives the
+ *                   pivot (any orthonormal basis of the remaining columns).
+ * desc (device, count x RQR_BATCH_DESC_LEN int64), per matrix:
+ *   {m, n, b, k, a_off, t_off, p_off, w_off, tv_off, g_off}: shape m x n
+ *   (1 <= n <= m <= max_m, n <= max_n, m <= 1024, n <= 512), block size
+ *   1 <= b <= max_b <= 32 (b + p <= 64), rank k (URV); element offsets of the
+ *   matrix in A (column-major, ld m), of its T (QRCP) or TU (URV) in T
+ *   (b x n, ld b), of its perm (QRCP, n int32) in perm, of its WV (URV, n x n,
+ *   ld n) in WV, of its TV (URV, b x n, ld b) in TV, of its Gaussians in G.
+ * order (device, optional) count int32: the queue order (e.g. longest first).
+ * A (device, in/out) float: R above, reflectors below, as rqrcp_factor.
+ * G (device, optional) float: per matrix the blocks G_i of l x (m - k0)
+ *   (QRCP: every block but the last, l = b + p; URV: every block, l = b), one
+ *   after another at g_off; NULL: drawn in the kernel, block i of matrix j
+ *   from the rqr_gauss_fill stream (seed, (j << 16) | i), rounded to FP32.
+ * work (device) rqr_batched_workspace_bytes bytes (a per-CTA scratch sized by
+ *   max_m, max_n, max_b). A matrix outside those limits is skipped and the
+ *   status word reads RQR_ERR_SIZE. The launch allocates nothing and, with
+ *   info == NULL, does not wait: it can be captured in a CUDA graph. */
+#define RQR_BATCH_QRCP 0
+#define RQR_BATCH_URV 1
+#define RQR_BATCH_DESC_LEN 10
+int rqr_batched_factor(rqr_handle_t h, int method, int count, const int64_t* desc, const int32_t* order, float* A,
+                       float* T, int32_t* perm, float* WV, float* TV, const float* G, int p, int q, uint64_t seed,
+                       int max_m, int max_n, int max_b, void* work, size_t lwork, int* info);
+int rqr_batched_workspace_bytes(int method, int count, int max_m, int max_n, int max_b, int p, size_t* bytes);
+
 /* Fills out[0:count] (device) with N(0,1) samples: element e is lane e%4 of
  * Philox4x32-10 block e/4 with counter {lo(e/4), hi(e/4), lo(stream),
  * hi(stream)} and key {lo(seed), hi(seed)}, through Box-Muller on the pairs

@@ -262,6 +262,12 @@ int qr_adjoint(const Ctx& c, int m, int n, int k, const double* Q1, int ldq, con
 // R (k x n) = upper triangle of the first k rows of F, zeros below.
 void copy_upper(const Ctx& c, int k, int n, const double* F, int ldf, double* R, int ldr);
 
+// Batched persistent factorizations of small FP32 matrices (batched.cu).
+size_t batched_workspace_bytes(int method, int count, int max_m, int max_n, int max_b, int p, int sms);
+int batched_factor(const Ctx& c, int method, int count, const long long* desc, const int* order, float* A, float* T,
+                   int32_t* perm, float* WV, float* TV, const float* G, int p, int q, uint64_t seed, int max_m,
+                   int max_n, int max_b, void* work, size_t lwork);
+
 // Context of a live handle (false for a NULL or destroyed handle).
 bool handle_ctx(rqr_handle_t h, Ctx* out);
 

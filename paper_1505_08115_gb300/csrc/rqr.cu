@@ -1007,6 +1007,49 @@ int rqr_copy_r(rqr_handle_t h, int k, int n, const void* F, int ldf, void* R, in
   return finish(h, nullptr);
 }
 
+int rqr_batched_workspace_bytes(int method, int count, int max_m, int max_n, int max_b, int p, size_t* bytes) {
+  if (method != RQR_BATCH_QRCP && method != RQR_BATCH_URV) return -1;
+  if (count < 0) return -2;
+  if (max_m < 1 || max_m > 1024) return -3;
+  if (max_n < 1 || max_n > max_m || max_n > 512) return -4;
+  if (max_b < 1 || max_b > 32) return -5;
+  if (p < 0 || max_b + p > 64 || (method == RQR_BATCH_URV && p != 0)) return -6;
+  if (!bytes) return -7;
+  int dev = 0, sms = rqr::kNumSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  *bytes = rqr::batched_workspace_bytes(method, count, max_m, max_n, max_b, p, sms);
+  return RQR_OK;
+}
+
+int rqr_batched_factor(rqr_handle_t h, int method, int count, const int64_t* desc, const int32_t* order, float* A,
+                       float* T, int32_t* perm, float* WV, float* TV, const float* G, int p, int q, uint64_t seed,
+                       int max_m, int max_n, int max_b, void* work, size_t lwork, int* info) {
+  if (!valid(h)) return -1;
+  if (method != RQR_BATCH_QRCP && method != RQR_BATCH_URV) return -2;
+  if (count < 0) return -3;
+  if (!desc && count > 0) return -4;
+  if (!A && count > 0) return -6;
+  if (!T && count > 0) return -7;
+  if (method == RQR_BATCH_QRCP && !perm && count > 0) return -8;
+  if (method == RQR_BATCH_URV && !WV && count > 0) return -9;
+  if (method == RQR_BATCH_URV && !TV && count > 0) return -10;
+  if (p < 0 || max_b + p > 64 || (method == RQR_BATCH_URV && p != 0)) return -12;
+  if (q < 0 || q > 64) return -13;
+  if (max_m < 1 || max_m > 1024) return -15;
+  if (max_n < 1 || max_n > max_m || max_n > 512) return -16;
+  if (max_b < 1 || max_b > 32) return -17;
+  if (!work && count > 0) return -18;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -18;
+  cudaGetLastError();
+  rqr::Ctx c = make_ctx(h);
+  cudaMemsetAsync(h->d_status, 0, sizeof(int), c.stream);
+  const int rc = rqr::batched_factor(c, method, count, reinterpret_cast<const long long*>(desc), order, A, T, perm, WV,
+                                     TV, G, p, q, seed, max_m, max_n, max_b, work, lwork);
+  if (rc != RQR_OK) return rc;
+  return finish(h, info);
+}
+
 const char* rqr_version(void) { return "rqr-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -164,6 +164,11 @@ def batch_shapes(count: int, seed: int = 1505, lo: int = 32, hi: int = 512):
     return [(int(a), int(b)) for a, b in zip(rows, cols)]
 
 
+def batch_matrix(m: int, n: int, seed: int, decay: float = 0.95) -> np.ndarray:
+    """N(0,1) entries scaled by the column-wise geometric decay decay^j (FP64)."""
+    return np.asfortranarray(rng(seed).standard_normal((m, n)) * decay ** np.arange(n))
+
+
 # ------------------------------------------------------------ GPU-side draws
 def _preload_torch_linalg():
     """torch loads its CUDA linear-algebra library lazily by name; under a

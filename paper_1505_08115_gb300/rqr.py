@@ -33,7 +33,8 @@ FORM_Q_NOALLOC_MAX_BYTES = 8 << 20
 EXPORTS = ("rqr_create", "rqr_destroy", "rqr_set_stream", "rqr_set_wait_limit_ns", "rqr_workspace_bytes",
            "rqrcp_factor", "rurv_factor",
            "rqr_form_q", "rqr_form_q_noalloc", "rqr_gemm", "rqr_gemm_workspace_bytes", "rqr_qr_adjoint",
-           "rqr_qr_adjoint_workspace_bytes", "rqr_copy_r", "rqr_gauss_fill",
+           "rqr_qr_adjoint_workspace_bytes", "rqr_copy_r", "rqr_batched_factor", "rqr_batched_workspace_bytes",
+           "rqr_gauss_fill",
            "rqr_philox_raw",
            "rqr_profile_enable", "rqr_profile_read", "rqr_profile_kernel_read", "rqr_version")
 PHASES = ("sketch", "pivot", "swap", "panel", "update", "downdate", "final", "right")
@@ -74,6 +75,8 @@ def load(path: str = SO_PATH):
         L.rqr_qr_adjoint.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i, vp, vp, i, vp, i, vp, i, vp, i, vp, sz, ip]
         L.rqr_qr_adjoint_workspace_bytes.argtypes = [i, i, i, ctypes.POINTER(sz)]
         L.rqr_copy_r.argtypes = [vp, i, i, vp, i, vp, i]
+        L.rqr_batched_factor.argtypes = [vp, i, i, vp, vp, vp, vp, vp, vp, vp, vp, i, i, u64, i, i, i, vp, sz, ip]
+        L.rqr_batched_workspace_bytes.argtypes = [i, i, i, i, i, i, ctypes.POINTER(sz)]
         L.rqr_gauss_fill.argtypes = [vp, u64, u64, i64, vp, i]
         L.rqr_philox_raw.argtypes = [vp, u32, u32, u32, u32, u32, i64, vp]
         L.rqr_profile_enable.argtypes = [vp, i]
@@ -313,6 +316,124 @@ def qr_adjoint(Q1: torch.Tensor, F: torch.Tensor, Qbar: torch.Tensor, Rbar: torc
     if rc > 0 or info.value:
         raise RQRError(f"rqr_qr_adjoint: {STATUS.get(rc or info.value, rc or info.value)}")
     return Abar
+
+
+BATCH_QRCP, BATCH_URV, BATCH_DESC_LEN = 0, 1, 10
+
+
+class BatchLayout:
+    """Packed storage of a batch of small column-major matrices (include/rqr.h,
+    rqr_batched_factor): element offsets of each matrix in A, of its T / TU,
+    perm, WV, TV and Gaussian blocks, and the per-matrix descriptor rows."""
+
+    def __init__(self, shapes, b, method=BATCH_QRCP, p=0, k=None):
+        import numpy as np
+
+        self.shapes = [(int(m), int(n)) for m, n in shapes]
+        cnt = len(self.shapes)
+        bs = [int(b)] * cnt if isinstance(b, int) else [int(x) for x in b]
+        ks = [0] * cnt if k is None else ([int(k)] * cnt if isinstance(k, int) else [int(x) for x in k])
+        self.method, self.p, self.b, self.k = method, p, bs, ks
+        desc = np.zeros((cnt, BATCH_DESC_LEN), dtype=np.int64)
+        a = t = pp = w = tv = g = 0
+        for i, ((m, n), bi, ki) in enumerate(zip(self.shapes, bs, ks)):
+            desc[i] = (m, n, bi, ki, a, t, pp, w, tv, g)
+            a += m * n
+            t += bi * n
+            pp += n
+            w += n * n if method == BATCH_URV else 0
+            tv += bi * n if method == BATCH_URV else 0
+            g += self.gauss_count(m, n, bi)
+        self.desc = desc
+        self.totals = {"A": a, "T": t, "perm": pp, "WV": w, "TV": tv, "G": g}
+        self.max_m = max((m for m, _ in self.shapes), default=1)
+        self.max_n = max((n for _, n in self.shapes), default=1)
+        self.max_b = max(bs, default=1)
+
+    def gauss_count(self, m, n, b):
+        """Values of the Gaussian blocks one matrix consumes (per block l x (m - k0))."""
+        l = b + self.p
+        tot, k0 = 0, 0
+        while k0 < n:
+            np_ = n - k0
+            if self.method == BATCH_QRCP and np_ <= b:
+                break
+            tot += l * (m - k0)
+            k0 += min(b, np_)
+        return tot
+
+    def longest_first(self):
+        """Queue order: matrices with the most work (m n^2) first."""
+        import numpy as np
+
+        w = np.array([m * n * n for m, n in self.shapes], dtype=np.float64)
+        return np.argsort(-w, kind="stable").astype(np.int32)
+
+    def pack(self, mats, device="cuda") -> torch.Tensor:
+        """The matrices (column-major float32) packed at their offsets."""
+        import numpy as np
+
+        flat = np.concatenate([np.asarray(M, dtype=np.float32).ravel(order="F") for M in mats]) if mats else \
+            np.zeros(0, np.float32)
+        return torch.from_numpy(flat).to(device)
+
+    def unpack(self, buf: torch.Tensor, key: str = "A"):
+        """Per-matrix views of a packed output (A, T, perm, WV, TV) as numpy arrays."""
+        import numpy as np
+
+        h = buf.cpu().numpy()
+        out = []
+        col = {"A": 4, "T": 5, "perm": 6, "WV": 7, "TV": 8}[key]
+        for i, (m, n) in enumerate(self.shapes):
+            off = int(self.desc[i, col])
+            r, c = {"A": (m, n), "T": (self.b[i], n), "perm": (n, 1), "WV": (n, n), "TV": (self.b[i], n)}[key]
+            v = h[off:off + r * c]
+            out.append(v.copy() if key == "perm" else v.reshape((r, c), order="F").copy())
+        return out
+
+
+def batched_factor(layout: BatchLayout, A: torch.Tensor, q: int = 0, seed: int = 1505, G: torch.Tensor | None = None,
+                   order: torch.Tensor | None = None, work: torch.Tensor | None = None, out=None, check: bool = True,
+                   desc: torch.Tensor | None = None):
+    """All matrices of the batch in one persistent launch (rqr_batched_factor).
+    A: packed float32 (layout.pack); returns a dict of packed outputs and info
+    (out["_keep"] = (desc, order, work): pass them back, with out=, to repeat
+    the launch without host-to-device copies, e.g. inside a CUDA-graph capture).
+    order: int32 queue order on the device (default longest first)."""
+    _require_cuda(A)
+    dev = A.device
+    L = load()
+    if order is None:
+        order = torch.from_numpy(layout.longest_first()).to(dev)
+    if desc is None:
+        desc = torch.from_numpy(layout.desc).to(dev)
+    tot = layout.totals
+    if out is None:
+        out = {"T": torch.empty(max(1, tot["T"]), dtype=torch.float32, device=dev)}
+        if layout.method == BATCH_QRCP:
+            out["perm"] = torch.empty(max(1, tot["perm"]), dtype=torch.int32, device=dev)
+        else:
+            out["WV"] = torch.empty(max(1, tot["WV"]), dtype=torch.float32, device=dev)
+            out["TV"] = torch.empty(max(1, tot["TV"]), dtype=torch.float32, device=dev)
+    if work is None:
+        sz = ctypes.c_size_t()
+        rc = L.rqr_batched_workspace_bytes(layout.method, len(layout.shapes), layout.max_m, layout.max_n,
+                                           layout.max_b, layout.p, ctypes.byref(sz))
+        if rc != 0:
+            raise RQRError(f"rqr_batched_workspace_bytes: argument {-rc} invalid")
+        work = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+    info = ctypes.c_int(0)
+    rc = L.rqr_batched_factor(handle(dev), layout.method, len(layout.shapes), _ptr(desc), _ptr(order), _ptr(A),
+                              _ptr(out["T"]), _ptr(out.get("perm")), _ptr(out.get("WV")), _ptr(out.get("TV")),
+                              _ptr(G), layout.p, q, seed, layout.max_m, layout.max_n, layout.max_b, _ptr(work),
+                              work.numel(), ctypes.byref(info) if check else None)
+    if rc < 0:
+        raise RQRError(f"rqr_batched_factor: argument {-rc} invalid")
+    if rc > 0:
+        raise RQRError(f"rqr_batched_factor: {STATUS.get(rc, rc)}")
+    out["info"] = info.value if check else None
+    out["_keep"] = (desc, order, work)
+    return out
 
 
 def gauss_fill(seed: int, stream: int, count: int, dtype=torch.float64, device="cuda") -> torch.Tensor:
