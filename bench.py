@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
                     help="mixed-precision modes timed on the same workload (comma list, '' for none)")
     ap.add_argument("--c4-svd", action="store_true", help="C4: sigma_i from the FP64 SVD of A (slow)")
-    ap.add_argument("--legs", default="c2,c4,cpu",
+    ap.add_argument("--legs", default="c2,c4,c5,cpu",
                     help="further measurements: c2 (8192^2 FP64 vs FP32), c4 (URV 8192^2, q = 0, 1, 2), "
-                         "cpu (LAPACK dgeqp3 and the single-threaded oracle)")
+                         "c5 (4096 small FP32 matrices, batched), cpu (LAPACK dgeqp3 and the single-threaded oracle)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the native FP64 path")
     ap.add_argument("--no-verify", action="store_true", help="skip the accuracy probe (profiling runs)")
     ap.add_argument("--seed", type=int, default=1505)
@@ -331,6 +331,100 @@ def leg_c4(a, dev, stream):
                                    "max": ratio.max().item()},
                 "offdiag_mass": (torch.linalg.norm(R - torch.diag(torch.diagonal(R))) / torch.linalg.norm(R)).item()}
         del work
+    return out
+
+
+def leg_c5(a, dev, stream):
+    """Config C5: 4096 FP32 matrices, rows uniform in [32, 512], cols = rows/2
+    rounded to 8, entries N(0,1) 0.95^j. One persistent launch each for the
+    batched randomized QRCP (p = 8) and the truncated URV (k = cols/4, q = 1),
+    block sizes from the autotuner's cache. Reported as matrices/s and GFLOP/s
+    (the flop models), against the single-matrix FP64 path (rqrcp_factor one
+    matrix at a time, timed on a sample of the same batch), with the residual
+    and orthogonality of a sample of the batch (FP64 on the CPU)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1505_08115_gb300 import autotune, inputs, rqr
+    from paper_1505_08115_gb300.flops import rqrcp_flops, rurv_flops
+
+    count = 4096
+    shapes = inputs.batch_shapes(count, seed=a.seed)
+    out = {"workload": f"{count} FP32 matrices, rows U[32, 512], cols rows/2 rounded to 8, N(0,1) 0.95^j"}
+    t0 = time.perf_counter()
+    bq = autotune.choose_b(shapes, rqr.BATCH_QRCP, p=8, q=0, device=dev)
+    bu = autotune.choose_b(shapes, rqr.BATCH_URV, p=0, q=1, device=dev)
+    out["autotune_s"] = time.perf_counter() - t0
+    out["b_chosen"] = {"qrcp": sorted(set(bq)), "urv": sorted(set(bu))}
+    g = torch.Generator(device=dev).manual_seed(a.seed + 8)
+    for method, bs, p, q in ((rqr.BATCH_QRCP, bq, 8, 0), (rqr.BATCH_URV, bu, 0, 1)):
+        ks = [max(1, n // 4) for _, n in shapes] if method == rqr.BATCH_URV else None
+        lay = rqr.BatchLayout(shapes, bs, method=method, p=p, k=ks)
+        cols = np.concatenate([0.95 ** np.arange(n) for _, n in shapes]).astype(np.float32)
+        rows = np.concatenate([[m] * n for m, n in shapes])
+        scale = torch.repeat_interleave(torch.from_numpy(cols).to(dev), torch.from_numpy(rows).to(dev))
+        A0 = torch.randn(lay.totals["A"], generator=g, device=dev, dtype=torch.float32) * scale
+        A = A0.clone()
+        res = rqr.batched_factor(lay, A, q=q, seed=a.seed + 9, check=False)
+
+        def call():
+            rqr.batched_factor(lay, A, q=q, seed=a.seed + 9, out=res, desc=res["_keep"][0], order=res["_keep"][1],
+                               work=res["_keep"][2], check=False)
+
+        ms = timed_calls(call, lambda: A.copy_(A0), max(2, a.steps), stream)
+        A.copy_(A0)
+        call()
+        torch.cuda.synchronize()
+        if method == rqr.BATCH_QRCP:
+            fl = sum(rqrcp_flops(m, n, b, p, resample=True)["total"] for (m, n), b in zip(shapes, bs))
+        else:
+            fl = sum(rurv_flops(m, n, b, 0, q, k)["total"] for (m, n), b, k in zip(shapes, bs, ks))
+        ent = {"ms": ms, "matrices_per_s": count / (ms / 1e3), "gflops": fl / (ms / 1e3) / 1e9,
+               "gpu_launches": 1}
+        # accuracy on a sample (every 128th matrix), FP64 on the CPU
+        sample = list(range(0, count, 128))
+        Ah = A0.cpu().numpy()
+        Fs = lay.unpack(A, "A")
+        Ts = lay.unpack(res["T"], "T")
+        if method == rqr.BATCH_QRCP:
+            Ps = lay.unpack(res["perm"], "perm")
+        else:
+            WVs, TVs = lay.unpack(res["WV"], "WV"), lay.unpack(res["TV"], "TV")
+        worst_res = worst_orth = 0.0
+        for i in sample:
+            m, n = shapes[i]
+            off = int(lay.desc[i, 4])
+            Ai = Ah[off:off + m * n].reshape((m, n), order="F").astype(np.float64)
+            F = Fs[i].astype(np.float64)
+            if method == rqr.BATCH_QRCP:
+                Q = oracle.form_q(F, Ts[i].astype(np.float64), bs[i])
+                r = np.linalg.norm(Ai[:, Ps[i]] - Q[:, :n] @ np.triu(F)[:n]) / np.linalg.norm(Ai)
+            else:
+                Q = oracle.form_q(F, Ts[i].astype(np.float64), bs[i])
+                P = oracle.form_q(WVs[i].astype(np.float64), TVs[i].astype(np.float64), bs[i])
+                k = ks[i]
+                r = np.linalg.norm((Ai @ P)[:, :k] - Q[:, :k] @ np.triu(F)[:k, :k]) / np.linalg.norm(Ai)
+            worst_res = max(worst_res, r)
+            worst_orth = max(worst_orth, np.linalg.norm(Q.T @ Q - np.eye(m)))
+        ent["sample_residual_max"] = worst_res
+        ent["sample_orthogonality_max"] = worst_orth
+        out["qrcp" if method == rqr.BATCH_QRCP else "urv_rank_cols/4_q1"] = ent
+        del A, A0, res
+    # the single-matrix FP64 path on a sample of the same shapes, one call each
+    sample = shapes[:: count // 64]
+    mats = [rqr.colmajor(torch.randn(m, n, generator=g, device=dev, dtype=torch.float64)) for m, n in sample]
+    works = [torch.empty(rqr.workspace_bytes(m, n, 16, 8), dtype=torch.uint8, device=dev) for m, n in sample]
+    for M, w in zip(mats, works):
+        rqr.rqrcp_factor(M.clone(), 16, 8, work=w, check=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for M, w in zip(mats, works):
+        rqr.rqrcp_factor(M, 16, 8, work=w, check=False)
+    torch.cuda.synchronize()
+    per = (time.perf_counter() - t0) / len(sample)
+    out["single_matrix_fp64_path"] = {"matrices_per_s": 1.0 / per, "sample": len(sample), "b": 16, "p": 8}
+    out["qrcp"]["speedup_vs_single_matrix_fp64"] = out["qrcp"]["matrices_per_s"] * per
     return out
 
 
@@ -660,6 +754,8 @@ def main():
             out["legs"]["c2"] = leg_c2(a, dev, stream)
         if "c4" in legs:
             out["legs"]["c4"] = leg_c4(a, dev, stream)
+        if "c5" in legs:
+            out["legs"]["c5"] = leg_c5(a, dev, stream)
         if "cpu" in legs:
             out["legs"]["cpu"] = leg_cpu(a)
 
