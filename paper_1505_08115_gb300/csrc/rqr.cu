@@ -105,6 +105,7 @@ struct RqrcpWs {
   char* pers;
   size_t part_cap;
   rqr::TcScratch tc;
+  rqr::TcScratch tcg;  // mixed modes (FP64 data): FP64X scratch of the Gram matrix V^T V
 };
 
 // Scratch of the tensor-core products: exponent maxima (FP64X), the operand
@@ -213,6 +214,11 @@ size_t carve_rqrcp(rqr::Carver& cv, int m, int n, int b, int p, int sms, RqrcpWs
                                std::min(tc_plane_units(tcm, nn, mm), kTcPlaneBudget));
     carve_tc(cv, tcm == RQR_FP64X ? (size_t)mm + nn + lb + 64 : 1, pa, pb, w.tc);
   }
+  w.tcg = rqr::TcScratch{};
+  if (is_mixed(tcm) && sizeof(T) == 8) {
+    const int mm = std::max(m, 1);
+    carve_tc(cv, (size_t)2 * b + 64, rqr::oztc_plane_elems(b, mm), rqr::oztc_plane_elems(b, mm), w.tcg);
+  }
   return cv.used;
 }
 
@@ -315,9 +321,17 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
     {
       Phase ph(h, RQR_PHASE_PANEL, 2.0 * mp * (double)b * b - 2.0 * b * (double)b * b / 3.0);
       panel_qr<T>(c, mp, b, P, lda, w.tau, w.pscr);
-      if (!emu) {
+      if (!emu && !w.tcg.pa) {
         make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
         gemm<T>(c, true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b, w.part, w.part_cap);
+      } else if (!emu) {
+        // mixed modes: the Gram matrix of V stays FP64-accurate (T's accuracy
+        // sets Q's orthogonality) through the FP64X digit products on V = E + L
+        const Gemm<T> gram_mm{c, RQR_FP64X, w.iscr, w.part, w.part_cap, &w.tcg};
+        make_vlow<T>(c, mp, b, P, lda, w.Vx, mp);
+        gram_mm(true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b);
+        gram_from_lower<T>(c, b, w.Vx, mp, w.gram, b);
+        make_vx<T>(c, mp, b, P, lda, w.Vx, mp);
       } else {
         make_vlow<T>(c, mp, b, P, lda, w.Vx, mp);
         mm(true, false, b, b, mp, T(1), w.Vx, mp, w.Vx, mp, T(0), w.gram, b);
@@ -332,7 +346,7 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       Phase ph(h, RQR_PHASE_UPDATE, 4.0 * mp * (double)n2 * b);
       if (!emu) {
         mm(true, false, b, n2, mp, T(1), w.Vx, mp, A2, lda, T(0), w.W, b);
-        gemm<T>(c, true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b, w.part, w.part_cap);
+        mm(true, false, b, n2, b, T(1), Tb, ldt, w.W, b, T(0), w.W2, b);
         mm(false, false, mp, n2, b, T(-1), w.Vx, mp, w.W2, b, T(1), A2, lda);
       } else {
         copy_mat<T>(c, b, n2, A2, lda, w.W, b);                              // E^T A2
@@ -579,7 +593,7 @@ int rurv_impl(rqr_handle_t h, int m, int n, double* A, int lda, int b, int p, in
       double* A2 = A + k0 + (size_t)(k0 + bi) * lda;
       if (!emu) {
         mm(true, false, bi, n2, mp, 1.0, w.Vx, mp, A2, lda, 0.0, w.W, bi);
-        gemm<double>(c, true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi, w.part, w.part_cap);
+        mm(true, false, bi, n2, bi, 1.0, Tb, ldtu, w.W, bi, 0.0, w.W2, bi);
         mm(false, false, mp, n2, bi, -1.0, w.Vx, mp, w.W2, bi, 1.0, A2, lda);
       } else {
         make_vlow<double>(c, mp, bi, X, lda, w.Vl, mp);

@@ -81,7 +81,8 @@ def test_workspace_bytes_sizes():
     0.2 GB in FP64 and 1.3 GB with the FP64X digit planes (the op(B) planes
     capped at 1 GiB per chunk); FP32 half of FP64 plus its 3xTF32 planes
     (8 bytes per element, chunk capped at 1 GiB); the mixed modes FP64's
-    buffers plus planes of 4 (TF32, 3xBF16) or 8 (3xTF32) bytes per element;
+    buffers plus planes of 4 (TF32, 3xBF16) or 8 (3xTF32) bytes per element
+    and the FP64X planes of the Gram matrix's two operands;
     the resampled sketch needs no more than the downdated one."""
     from paper_1505_08115_gb300 import rqr
     L = rqr.load()
@@ -93,9 +94,10 @@ def test_workspace_bytes_sizes():
     planes8 = 2 ** 30 + 8 * l * n   # op(B) chunk + op(A) planes of G
     rc, w32 = _ws(L, n, n, 128, 8, prec=rqr.FP32)
     assert rc == 0 and abs(w32 - w64 / 2 - planes8) <= 0.02 * w64
+    gram = 2 * 16 * 128 * n  # FP64X digit planes of V^T and V for the FP64-accurate Gram matrix
     for prec, bpe in ((rqr.TF32, 4), (rqr.BF16X3, 4), (rqr.TF32X3, 8)):
         rc, wm = _ws(L, n, n, 128, 8, prec=prec)
-        assert rc == 0 and abs(wm - w64 - min(2 ** 30, bpe * n * n) - bpe * l * n) <= 0.02 * w64, (prec, wm)
+        assert rc == 0 and abs(wm - w64 - min(2 ** 30, bpe * n * n) - bpe * l * n - gram) <= 0.02 * w64, (prec, wm)
     assert _ws(L, 16384, 16384, 128, 8, sketch=1)[1] <= w64
     sizes = [_ws(L, n, n, 128, 8)[1] for n in (256, 1000, 4096, 8192, 16384)]
     assert sizes == sorted(sizes)
