@@ -76,19 +76,127 @@ __device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* s
   return s_ok != 0;
 }
 
+// ------------------------------------------------------------ flagged words
+// The pivot kernel exchanges its values as 8-byte words that carry 32 bits of
+// data and a 32-bit tag (the step + 1): one 64-bit store is seen whole or not
+// at all, so a reader that finds the step's tag in a word has that word's
+// data, without a fence or an arrival counter. A double takes two words
+// (low, high half), a float one. The words are zeroed before every launch, so
+// no stale word carries a tag of the launch.
+typedef unsigned long long llw;
+
+__device__ __forceinline__ void ll_store(llw* w, uint32_t data, uint32_t tag) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(w), "l"(((llw)tag << 32) | data) : "memory");
+}
+__device__ __forceinline__ llw ll_load(const llw* w) {
+  llw v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+  return v;
+}
+// Waits until the word carries `tag`; false when the wait limit ran out or
+// the CTA was told to give up (*fail set by another thread).
+__device__ __forceinline__ bool ll_wait(const llw* w, uint32_t tag, uint32_t& data, unsigned long long limit_ns,
+                                        volatile int* fail) {
+  llw v = ll_load(w);
+  if ((uint32_t)(v >> 32) != tag) {
+    const uint64_t t0 = gtime_ns();
+    while ((uint32_t)((v = ll_load(w)) >> 32) != tag) {
+      if (*fail || gtime_ns() - t0 > limit_ns) {
+        *fail = 1;
+        return false;
+      }
+    }
+  }
+  data = (uint32_t)v;
+  return true;
+}
+
+// Two adjacent words (16-byte aligned) with one vector load: the two halves
+// arrive together instead of one L2 round trip after the other.
+__device__ __forceinline__ void ll_load2(const llw* w, llw& x, llw& y) {
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "l"(w) : "memory");
+}
+// Waits until both words at w (16-byte aligned) carry `tag`.
+__device__ __forceinline__ bool ll_wait2(const llw* w, uint32_t tag, uint32_t& d0, uint32_t& d1,
+                                         unsigned long long limit_ns, volatile int* fail) {
+  llw x, y;
+  ll_load2(w, x, y);
+  if ((uint32_t)(x >> 32) != tag || (uint32_t)(y >> 32) != tag) {
+    const uint64_t t0 = gtime_ns();
+    while (true) {
+      ll_load2(w, x, y);
+      if ((uint32_t)(x >> 32) == tag && (uint32_t)(y >> 32) == tag) break;
+      if (*fail || gtime_ns() - t0 > limit_ns) {
+        *fail = 1;
+        return false;
+      }
+    }
+  }
+  d0 = (uint32_t)x;
+  d1 = (uint32_t)y;
+  return true;
+}
+
+// Waits until the four words of a 32-byte slot carry `tag` (two vector loads
+// issued together per try).
+__device__ __forceinline__ bool ll_wait4(const llw* w, uint32_t tag, uint32_t d[4], unsigned long long limit_ns,
+                                         volatile int* fail) {
+  llw x[4];
+  auto ready = [&]() {
+    ll_load2(w, x[0], x[1]);
+    ll_load2(w + 2, x[2], x[3]);
+    return (uint32_t)(x[0] >> 32) == tag && (uint32_t)(x[1] >> 32) == tag && (uint32_t)(x[2] >> 32) == tag &&
+           (uint32_t)(x[3] >> 32) == tag;
+  };
+  if (!ready()) {
+    const uint64_t t0 = gtime_ns();
+    while (!ready()) {
+      if (*fail || gtime_ns() - t0 > limit_ns) {
+        *fail = 1;
+        return false;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = (uint32_t)x[i];
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void ll_put(llw* w, T x, uint32_t tag) {
+  if constexpr (sizeof(T) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    ll_store(w, (uint32_t)b, tag);
+    ll_store(w + 1, (uint32_t)(b >> 32), tag);
+  } else {
+    ll_store(w, __float_as_uint(x), tag);
+  }
+}
+template <typename T>
+__device__ __forceinline__ bool ll_get(const llw* w, uint32_t tag, T& x, unsigned long long limit_ns,
+                                       volatile int* fail) {
+  uint32_t lo = 0, hi = 0;
+  if constexpr (sizeof(T) == 8) {
+    if (!ll_wait2(w, tag, lo, hi, limit_ns, fail)) return false;
+    x = __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+  } else {
+    if (!ll_wait(w, tag, lo, limit_ns, fail)) return false;
+    x = __uint_as_float(lo);
+  }
+  return true;
+}
+
 template <typename T>
 struct PArgs {
   int l, np, per, bsteps;
   const T* Y;
   int ldy;
   int* picks;
-  long long* cand_k;  // [2][C] candidate keys (step parity)
-  int* cand_p;  // [2][C] candidate positions
-  T* candcol;   // [2][C][l] candidate columns
-  T* colbuf;    // [2][l + 2] column leaving the pivot position, its norm and reference norm
-  GridSync* gs;
+  llw* slots;   // [2][C][4] per CTA and step parity: key low, key high, position (flagged words)
+  llw* col;     // [2][C][2 l] each CTA's candidate column, rows s.. (flagged words)
+  llw* colbuf;  // [2][2 (l + 2)] the column leaving the pivot position, its norm and reference norm
   int* status;
-  unsigned long long wait_ns;  // limit of each arrival wait
+  unsigned long long wait_ns;  // limit of each wait for another CTA's words
 };
 
 // Candidates compare by key: the bit pattern of a squared norm (>= 0) as a
@@ -108,11 +216,12 @@ __device__ __forceinline__ bool better(long long k, int p, long long bk, int bp)
 }
 
 // b steps of Fig. QR on the sketch. Per step s every CTA publishes its best
-// remaining column (squared norm of rows s.., position, values), meets the
-// others at the arrival barrier, and then picks the global winner itself from
-// the C published candidates (same data and order in every CTA, so the same
-// winner), builds the reflector from the winner's values and applies it to its
-// own columns. One barrier per step and no serial phase in a single CTA.
+// remaining column (squared norm of rows s.., position, values) as flagged
+// words, waits for the C published candidates (one thread per CTA slot), picks
+// the global winner itself (same data and order in every CTA, so the same
+// winner), reads the winner's values, builds the reflector and applies it to
+// its own columns. Two L2 round trips per step (the slots, then the winner's
+// column), no grid barrier, no fence, and no serial phase in a single CTA.
 // The squared norms of rows s+1.. are downdated from those of rows s..
 // (the reflector keeps the norm of rows s..: |y(s+1:)|^2 = |y(s:)|^2 - y_s^2,
 // y_s after the update) and recomputed exactly from the column whenever the
@@ -132,10 +241,12 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   __shared__ int shp[PNW], shq[PNW];
   __shared__ T s_tau;
   __shared__ int s_win, s_pos;
+  __shared__ volatile int s_fail;  // a wait of this CTA gave up: the others stop waiting too
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // an earlier step of this call failed: nothing here may be trusted (every
   // CTA reads the same word before any of them can change it)
   if (*(volatile int*)a.status != 0) return;
+  if (tid == 0) s_fail = 0;
   const int lo = q * a.per, hi = min(a.np, lo + a.per), cnt = max(0, hi - lo);
   for (int e = tid; e < cnt * l; e += PT) {
     const int pl = e / l, r = e % l;
@@ -183,31 +294,49 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
         bn = shn[w];
         bp = shp[w];
       }
+    const uint32_t tag = (uint32_t)s + 1u;
     if (tid == 0) {
-      a.cand_k[par * C + q] = bn;
-      a.cand_p[par * C + q] = bp;
+      llw* sl = a.slots + ((size_t)par * C + q) * 4;
+      ll_store(sl, (uint32_t)(unsigned long long)bn, tag);
+      ll_store(sl + 1, (uint32_t)((unsigned long long)bn >> 32), tag);
+      ll_store(sl + 2, (uint32_t)bp, tag);
+      ll_store(sl + 3, 0u, tag);
     }
     if (bp >= lo && bp < hi)
-      for (int r = s + tid; r < l; r += PT) a.candcol[((size_t)par * C + q) * l + r] = tile[(size_t)(bp - lo) * LS + r];
+      for (int r = s + tid; r < l; r += PT)
+        ll_put<T>(a.col + ((size_t)par * C + q) * 2 * l + 2 * r, tile[(size_t)(bp - lo) * LS + r], tag);
     if (s >= lo && s < hi) {
-      for (int r = s + tid; r < l; r += PT) a.colbuf[(size_t)par * LB + r] = tile[(size_t)(s - lo) * LS + r];
+      llw* cb = a.colbuf + (size_t)par * 2 * LB;
+      for (int r = s + tid; r < l; r += PT) ll_put<T>(cb + 2 * r, tile[(size_t)(s - lo) * LS + r], tag);
       if (tid == 0) {
-        a.colbuf[(size_t)par * LB + l] = nrm[s - lo];
-        a.colbuf[(size_t)par * LB + l + 1] = ref[s - lo];
+        ll_put<T>(cb + 2 * l, nrm[s - lo], tag);
+        ll_put<T>(cb + 2 * (l + 1), ref[s - lo], tag);
       }
     }
-    if (!count_barrier(&a.gs->count, (unsigned)C * (unsigned)(s + 1), &a.gs->err, a.status, a.wait_ns)) return;
-    // ---- global winner (every CTA, identical order)
+    // ---- global winner (every CTA, identical order): thread t waits for CTA
+    // t's slot words of this step; no barrier, no fence, no counter
     long long cn = -1;
     int cp = 0x7fffffff, cq = 0;
-    for (int t = tid; t < C; t += PT) {
-      const long long n = __ldcg(a.cand_k + par * C + t);
-      const int pp = __ldcg(a.cand_p + par * C + t);
-      if (better(n, pp, cn, cp)) {
+    bool bad = false;
+    for (int t = tid; t < C && !bad; t += PT) {
+      const llw* sl = a.slots + ((size_t)par * C + t) * 4;
+      // key halves and position in one 32-byte slot: two vector loads in flight together
+      uint32_t d[4];
+      if (!ll_wait4(sl, tag, d, a.wait_ns, &s_fail)) {
+        bad = true;
+        break;
+      }
+      const uint32_t k0 = d[0], k1 = d[1], pp = d[2];
+      const long long n = (long long)(((unsigned long long)k1 << 32) | k0);
+      if (better(n, (int)pp, cn, cp)) {
         cn = n;
-        cp = pp;
+        cp = (int)pp;
         cq = t;
       }
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) atomicCAS(a.status, 0, RQR_ERR_TIMEOUT);
+      return;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -241,37 +370,56 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
     }
     __syncthreads();
     const int qj = s_win, pw = s_pos;  // winning CTA and position (the same in every CTA)
-    const T* ycol = a.candcol + ((size_t)par * C + qj) * l;
+    const llw* ycol = a.col + ((size_t)par * C + qj) * 2 * l;
     const int L = l - s;
+    // the winner's rows s.. into v, and the column leaving position s into the
+    // winner's position when this CTA owns it
+    for (int r = tid; r < L && !bad; r += PT) {
+      T x;
+      if (!ll_get<T>(ycol + 2 * (s + r), tag, x, a.wait_ns, &s_fail)) bad = true;
+      else v[r] = x;
+    }
+    if (pw != s && pw >= lo && pw < hi) {
+      const llw* cb = a.colbuf + (size_t)par * 2 * LB;
+      for (int r = s + tid; r < l && !bad; r += PT) {
+        T x;
+        if (!ll_get<T>(cb + 2 * r, tag, x, a.wait_ns, &s_fail)) bad = true;
+        else tile[(size_t)(pw - lo) * LS + r] = x;
+      }
+      if (tid == 0 && !bad) {
+        T x1, x2;
+        if (ll_get<T>(cb + 2 * l, tag, x1, a.wait_ns, &s_fail) && ll_get<T>(cb + 2 * (l + 1), tag, x2, a.wait_ns, &s_fail)) {
+          nrm[pw - lo] = x1;
+          ref[pw - lo] = x2;
+        } else {
+          bad = true;
+        }
+      }
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) atomicCAS(a.status, 0, RQR_ERR_TIMEOUT);
+      return;
+    }
     if (warp == 0) {
       // reflector of rows s.. of the winner (Sec. 3.1, sign(0) = +1)
       T ss = T(0);
       for (int r = lane; r < L; r += 32) {
-        const T x = __ldcg(ycol + s + r);
-        v[r] = x;
+        const T x = v[r];
         ss += x * x;
       }
       ss = warp_sum(ss);
-      const T alpha = __ldcg(ycol + s);
-      T tau = T(0), d = T(1);
+      const T alpha = v[0];
+      T tau = T(0), rd = T(1);
       if (L >= 2 && ss > T(0)) {
         const T beta = -sgn0(alpha) * sqrt(ss);
-        d = alpha - beta;
+        rd = T(1) / (alpha - beta);  // one division per step: FP64 division is slow on GB300
         tau = (beta - alpha) / beta;
       }
       __syncwarp();
-      for (int r = 1 + lane; r < L; r += 32) v[r] = tau == T(0) ? T(0) : v[r] / d;
+      for (int r = 1 + lane; r < L; r += 32) v[r] = tau == T(0) ? T(0) : v[r] * rd;
       if (lane == 0) {
         v[0] = T(1);
         s_tau = tau;
-      }
-    } else if (pw != s && pw >= lo && pw < hi) {
-      // the column that was at position s moves to the winner's position
-      for (int r = s + tid - 32; r < l; r += PT - 32)
-        tile[(size_t)(pw - lo) * LS + r] = __ldcg(a.colbuf + (size_t)par * LB + r);
-      if (tid == 32) {
-        nrm[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l);
-        ref[pw - lo] = __ldcg(a.colbuf + (size_t)par * LB + l + 1);
       }
     }
     __syncthreads();
@@ -567,10 +715,16 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
   return sizeof(double) * ((size_t)per * (l | 1) + l + 2 * (size_t)per);
 }
 
+// Flagged words of the pivot exchange: slots [2][C][4], candidate columns
+// [2][C][2 l], the column leaving the pivot position [2][2 (l + 2)].
+static size_t ypick_exchange_words(int l, int C) {
+  return 2 * (size_t)C * 4 + 2 * (size_t)C * 2 * l + 2 * 2 * ((size_t)l + 2);
+}
+
 size_t ypick_persist_scratch_bytes(int l, int np, int sms) {
   int C, per;
   persist_smem(l, np, sms, C, per);
-  return 64 + sizeof(double) * (2 * (size_t)C * (l + 1) + 2 * (size_t)l + 16) + sizeof(int) * 2 * (size_t)C + 256;
+  return sizeof(unsigned long long) * ypick_exchange_words(l, C) + 256;
 }
 
 // Returns false (and queues nothing) when the sketch slice does not fit in
@@ -593,15 +747,13 @@ bool ypick_persist(const Ctx& c, int l, int np, int bsteps, const T* Y, int ldy,
     cudaGetLastError();
     return false;
   }
-  char* p = static_cast<char*>(scratch);
-  GridSync* gs = reinterpret_cast<GridSync*>(p);
-  p += 64;
-  long long* cand_k = reinterpret_cast<long long*>(p);
-  T* candcol = reinterpret_cast<T*>(cand_k + 2 * (size_t)C);
-  T* colbuf = candcol + 2 * (size_t)C * l;
-  int* cand_p = reinterpret_cast<int*>(colbuf + 2 * (size_t)(l + 2) + 8);
-  cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, cand_k, cand_p, candcol, colbuf, gs, c.status, c.wait_ns};
+  // zeroed before every launch: no word carries a tag of this launch until written by it
+  llw* w = static_cast<llw*>(scratch);
+  cudaMemsetAsync(w, 0, sizeof(llw) * ypick_exchange_words(l, C), c.stream);
+  llw* slots = w;
+  llw* col = slots + 2 * (size_t)C * 4;
+  llw* colbuf = col + 2 * (size_t)C * 2 * l;
+  PArgs<T> a{l, np, per, bsteps, Y, ldy, picks, slots, col, colbuf, c.status, c.wait_ns};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_ypick_persist<T>, dim3(C), dim3(PT), args, smem, c.stream) !=
       cudaSuccess) {
