@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--b", type=int, default=128)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
-    ap.add_argument("--prec", default="fp64x", choices=["fp64", "fp64x"],
-                    help="fp64: FP64 DMMA products; fp64x: FP64-accurate bf16 tensor-core products")
+    ap.add_argument("--prec", default="fp64x", choices=["fp64", "fp64x", "tf32", "3xbf16", "3xtf32"],
+                    help="headline precision: fp64 (DMMA products), fp64x (FP64-accurate bf16 tensor-core "
+                         "products), or a mixed mode (profiling runs)")
     ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
                     help="mixed-precision modes timed on the same workload (comma list, '' for none)")
     ap.add_argument("--c4-svd", action="store_true", help="C4: sigma_i from the FP64 SVD of A (slow)")
@@ -581,7 +582,7 @@ def main():
     T = rqr.empty_colmajor(b, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     modes = [x for x in a.modes.split(",") if x]
-    work = torch.empty(max(rqr.workspace_bytes(n, n, b, p, -1, rqr.PRECISIONS[x], sk) for x in ["fp64x"] + modes),
+    work = torch.empty(max(rqr.workspace_bytes(n, n, b, p, -1, rqr.PRECISIONS[x], sk) for x in [a.prec] + modes),
                        dtype=torch.uint8, device=dev)
     seed = a.seed + 1 + rank
     stream = torch.cuda.current_stream(dev)
