@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--b", type=int, default=128)
+    ap.add_argument("--b", type=int, default=0, help="block size; 0: chosen by the autotuner from 64, 128, 192, 256")
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--sketch", default="downdate", choices=["downdate", "resample"])
     ap.add_argument("--prec", default="fp64x", choices=["fp64", "fp64x", "tf32", "3xbf16", "3xtf32"],
@@ -509,6 +509,8 @@ def run_reference(a, rank):
     """Reference arm: the CPU oracle as it stands, bounded samples of the workload."""
     if rank != 0:
         return
+    if a.b <= 0:
+        a.b = 128  # the block size the GPU arm's autotuner picks on GB300 (64/128/192/256 measured)
     import numpy as np
     import torch
 
@@ -575,9 +577,16 @@ def main():
     rqr.load()  # fails loudly when the CUDA library is missing
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    n, b, p = a.n, a.b, a.p
+    n, p = a.n, a.p
     sk = rqr.SKETCH_DOWNDATE if a.sketch == "downdate" else rqr.SKETCH_RESAMPLE
     A0 = make_matrix(n, a.seed + rank, dev)
+    b_tuning = None
+    if a.b <= 0:
+        # b from {64, 128, 192, 256} by the autotuner (cached per device model)
+        from paper_1505_08115_gb300 import autotune
+
+        a.b, b_tuning = autotune.choose_block(A0, prec=a.prec, p=p)
+    b = a.b
     A = rqr.empty_colmajor(n, n, torch.float64, dev)
     T = rqr.empty_colmajor(b, n, torch.float64, dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
@@ -676,7 +685,8 @@ def main():
                              "X: 4 random vectors; ||A||_2 by power iteration",
            "phases": {k: {"ms": v["ms"] / a.steps, "gflops": (v["flops"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else 0,
                           "launches": v["launches"] // a.steps} for k, v in prof.items()},
-           "roofline": roof, "gpu_launches": launches, "clocks": head["clocks"]}
+           "roofline": roof, "gpu_launches": launches, "clocks": head["clocks"],
+           "block_size_tuning_ms": b_tuning}
     step = head["step"]
 
     if a.prec != "fp64" and not a.no_fp64_compare:

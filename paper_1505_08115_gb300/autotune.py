@@ -98,3 +98,46 @@ def choose_b(shapes, method: int = rqr.BATCH_QRCP, p: int = 8, q: int = 0, candi
             json.dump(cache, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
     return [int(cache[_key(method, *size_class(m, n), sms, p, q)]["b"]) for m, n in shapes]
+
+
+def choose_block(A: torch.Tensor, prec="fp64x", p: int = 8, candidates=(64, 128, 192, 256), seed: int = 1505,
+                 path: str | None = None) -> tuple[int, dict]:
+    """Block size b of one large factorization (rqrcp_factor, DOWNDATE): each
+    candidate is timed on a copy of A (one untimed call, then one timed with
+    CUDA events); the fastest is cached under (m, n, precision, SM count, p).
+    Returns (b, {b: ms}) ({} when the choice came from the cache)."""
+    m, n = A.shape
+    sms = torch.cuda.get_device_properties(A.device).multi_processor_count
+    path = cache_path() if path is None else path
+    cache = _load(path)
+    key = f"rqrcp|m{m}|n{n}|{prec}|sm{sms}|p{p}"
+    if key in cache:
+        return int(cache[key]["b"]), {}
+    work = None
+    times = {}
+    X = rqr.empty_colmajor(m, n, A.dtype, A.device)
+    stream = torch.cuda.current_stream(A.device)
+    for b in candidates:
+        if b > n:
+            continue
+        need = rqr.workspace_bytes(m, n, b, p, -1, rqr.PRECISIONS[prec])
+        if work is None or work.numel() < need:
+            work = torch.empty(need, dtype=torch.uint8, device=A.device)
+        T = rqr.empty_colmajor(b, n, A.dtype, A.device)
+        perm = torch.empty(n, dtype=torch.int32, device=A.device)
+        X.copy_(A)
+        rqr.rqrcp_factor(X, b, p, seed=seed, T=T, perm=perm, work=work, check=False, prec=prec)
+        X.copy_(A)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rqr.rqrcp_factor(X, b, p, seed=seed, T=T, perm=perm, work=work, check=False, prec=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[b] = e0.elapsed_time(e1)
+    best = min(times, key=times.get)
+    cache[key] = {"b": best, "ms": times}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best, times
