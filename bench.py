@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
                     help="mixed-precision modes timed on the same workload (comma list, '' for none)")
     ap.add_argument("--c4-svd", action="store_true", help="C4: sigma_i from the FP64 SVD of A (slow)")
+    ap.add_argument("--c5-count", type=int, default=4096, help="C5: matrices in the batch")
     ap.add_argument("--legs", default="c2,c4,c5,cpu",
                     help="further measurements: c2 (8192^2 FP64 vs FP32), c4 (URV 8192^2, q = 0, 1, 2), "
                          "c5 (4096 small FP32 matrices, batched), cpu (LAPACK dgeqp3 and the single-threaded oracle)")
@@ -350,7 +351,7 @@ def leg_c5(a, dev, stream):
     from paper_1505_08115_gb300 import autotune, inputs, rqr
     from paper_1505_08115_gb300.flops import rqrcp_flops, rurv_flops
 
-    count = 4096
+    count = a.c5_count
     shapes = inputs.batch_shapes(count, seed=a.seed)
     out = {"workload": f"{count} FP32 matrices, rows U[32, 512], cols rows/2 rounded to 8, N(0,1) 0.95^j"}
     t0 = time.perf_counter()
@@ -384,7 +385,7 @@ def leg_c5(a, dev, stream):
         ent = {"ms": ms, "matrices_per_s": count / (ms / 1e3), "gflops": fl / (ms / 1e3) / 1e9,
                "gpu_launches": 1}
         # accuracy on a sample (every 128th matrix), FP64 on the CPU
-        sample = list(range(0, count, 128))
+        sample = list(range(0, count, max(1, count // 32)))
         Ah = A0.cpu().numpy()
         Fs = lay.unpack(A, "A")
         Ts = lay.unpack(res["T"], "T")
@@ -413,7 +414,7 @@ def leg_c5(a, dev, stream):
         out["qrcp" if method == rqr.BATCH_QRCP else "urv_rank_cols/4_q1"] = ent
         del A, A0, res
     # the single-matrix FP64 path on a sample of the same shapes, one call each
-    sample = shapes[:: count // 64]
+    sample = shapes[:: max(1, count // 64)]
     mats = [rqr.colmajor(torch.randn(m, n, generator=g, device=dev, dtype=torch.float64)) for m, n in sample]
     works = [torch.empty(rqr.workspace_bytes(m, n, 16, 8), dtype=torch.uint8, device=dev) for m, n in sample]
     for M, w in zip(mats, works):

@@ -248,7 +248,6 @@ __global__ void k_build_map(int kb, int np, const int* picks, int* imap, int* st
   for (int e = threadIdx.x; e < kb; e += blockDim.x) cont[e] = e;
   for (int e = threadIdx.x; e < kMapHash; e += blockDim.x) hkey[e] = -1;
   __syncthreads();
-  if (threadIdx.x != 0) return;
   auto slot = [&](int p) -> int* {
     if (p < kb) return cont + p;
     unsigned h = ((unsigned)p * 2654435761u) & (kMapHash - 1);
@@ -259,29 +258,36 @@ __global__ void k_build_map(int kb, int np, const int* picks, int* imap, int* st
     }
     return hval + h;
   };
-  for (int j = 0; j < kb; ++j) {
-    const int pk = picks[j];
-    if (pk == j) continue;
-    int* a = slot(j);
-    int* b = slot(pk);
-    const int t = *a;
-    *a = *b;
-    *b = t;
-  }
-  int n = 0;
-  for (int e = 0; e < kb; ++e)
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kb; ++j) {
+      const int pk = picks[j];
+      if (pk == j) continue;
+      int* a = slot(j);
+      int* b = slot(pk);
+      const int t = *a;
+      *a = *b;
+      *b = t;
+    }
+  __syncthreads();
+  // emit the moved positions with all threads (the pairs are independent, so
+  // their order in imap does not matter)
+  __shared__ int s_n;
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kb; e += blockDim.x)
     if (cont[e] != e) {
-      imap[1 + 2 * n] = e;
-      imap[2 + 2 * n] = cont[e];
-      ++n;
+      const int t = atomicAdd(&s_n, 1);
+      imap[1 + 2 * t] = e;
+      imap[2 + 2 * t] = cont[e];
     }
-  for (int h = 0; h < kMapHash; ++h)
+  for (int h = threadIdx.x; h < kMapHash; h += blockDim.x)
     if (hkey[h] != -1 && hval[h] != hkey[h]) {
-      imap[1 + 2 * n] = hkey[h];
-      imap[2 + 2 * n] = hval[h];
-      ++n;
+      const int t = atomicAdd(&s_n, 1);
+      imap[1 + 2 * t] = hkey[h];
+      imap[2 + 2 * t] = hval[h];
     }
-  imap[0] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) imap[0] = s_n;
 }
 
 template <typename T>

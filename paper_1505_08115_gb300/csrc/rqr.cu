@@ -162,7 +162,10 @@ struct Gemm {
   const rqr::TcScratch* tc;  // null: no tensor-core scratch (FP64X: the mma.sync splitting only)
   void operator()(bool ta, bool tb, int M, int N, int K, T alpha, const T* A, int lda, const T* B, int ldb, T beta,
                   T* C, int ldc) const {
-    const bool big = (double)M * N * K >= 4.0e6 && M >= 16 && N >= 16 && K >= 16;
+    // products from about 1e6 multiply-adds up go to the tensor cores: below
+    // that the splitting costs more than it saves; above it the FP64 pipe is
+    // slower (e.g. the downdate's l x b x b product on a few CTAs: 160 us)
+    const bool big = (double)M * N * K >= 1.0e6 && M >= 16 && N >= 16 && K >= 16;
     if (mode && big) {
       if constexpr (sizeof(T) == 8) {
         if (mode == RQR_FP64X) {
@@ -361,12 +364,12 @@ int rqrcp_impl(rqr_handle_t h, int m, int n, T* A, int lda, int b, int p, uint64
       T* Gk = w.Gc + (size_t)k0 * l;
       if (!emu) {
         mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(0), w.GV, l);
-        gemm<T>(c, false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l, w.part, w.part_cap);
+        mm(false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l);
         mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);
       } else {
         copy_mat<T>(c, l, b, Gk, l, w.GV, l);                                  // G E
         mm(false, false, l, b, mp, T(1), Gk, l, w.Vx, mp, T(1), w.GV, l);      // + G L
-        gemm<T>(c, false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l, w.part, w.part_cap);
+        mm(false, false, l, b, b, T(1), w.GV, l, Tb, ldt, T(0), w.GVT, l);
         mm(false, true, l, mp, b, T(-1), w.GVT, l, w.Vx, mp, T(1), Gk, l);     // - GVT L^T
         add_mat<T>(c, l, b, T(-1), w.GVT, l, Gk, l);                           // - GVT E^T
       }

@@ -195,6 +195,41 @@ __global__ void __launch_bounds__(256) k_mix_split_strided(int R, int K, const I
   }
 }
 
+// ------------------------------------------------------------------ epilogue arithmetic
+// The FP64 value of an FP32 accumulator, from its bit pattern with integer
+// operations (exact, subnormals included): GB300 runs the FP32 -> FP64
+// conversion on its narrow FP64 pipe, where it doubled the epilogue's FP64
+// work (measured: FP64 pipe 79% busy in the trailing update).
+__device__ __forceinline__ double f32_to_f64(uint32_t u) {
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (e == 0xFFu) {
+    bits = s | (0x7FFull << 52) | ((unsigned long long)m << 29);
+  } else if (e != 0) {
+    bits = s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0) {
+    bits = s;
+  } else {
+    const int sh = __clz(m) - 8;  // m << sh has its leading bit at position 23
+    bits = s | ((unsigned long long)(897 - sh) << 52) | ((unsigned long long)((m << sh) & 0x7FFFFFu) << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+template <typename CT>
+__device__ __forceinline__ CT acc_value(uint32_t u) {
+  if constexpr (sizeof(CT) == 8) return f32_to_f64(u);
+  else return __uint_as_float(u);
+}
+
+// -x by flipping the sign bit (an integer operation, exact)
+template <typename CT>
+__device__ __forceinline__ CT neg_value(CT x) {
+  if constexpr (sizeof(CT) == 8) return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63));
+  else return __int_as_float(__float_as_int(x) ^ (int)0x80000000u);
+}
+
 // ------------------------------------------------------------------ product kernel
 template <typename CT>
 struct MixArgs {
@@ -371,12 +406,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             for (int c = 0; c < MX_CLD; ++c) {
               const int j = jb + c;
               if (j >= a.N) continue;
-              const CT x = (CT)__uint_as_float(v[g + c]);
+              const CT x = acc_value<CT>(v[g + c]);
               CT* cp = a.C + i + (size_t)j * a.ldc;
               switch (mode) {
                 case 0: a.part[(size_t)(t % a.S) * a.M * a.N + i + (size_t)j * a.M] = x; break;
                 case 1: *cp = x; break;
-                case 2: *cp = -x; break;
+                case 2: *cp = neg_value<CT>(x); break;
                 case 3: *cp = cold[c] + x; break;
                 case 4: *cp = cold[c] - x; break;
                 case 5: *cp = a.alpha * x; break;
