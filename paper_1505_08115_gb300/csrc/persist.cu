@@ -236,10 +236,11 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   T* v = tile + (size_t)a.per * LS;           // [l]
   T* nrm = v + l;                             // [per] squared norm of rows s.. of each column
   T* ref = nrm + a.per;                       // [per] the last exactly computed squared norm
+  T* dsh = ref + a.per;                       // [per] phase-A dot products of a step
   const int LB = l + 2;                       // colbuf stride: values, norm, reference
   __shared__ long long shn[PNW];
   __shared__ int shp[PNW], shq[PNW];
-  __shared__ T s_tau;
+  __shared__ T s_tau, s_rd;
   __shared__ int s_win, s_pos;
   __shared__ volatile int s_fail;  // a wait of this CTA gave up: the others stop waiting too
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -400,82 +401,111 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       if (tid == 0) atomicCAS(a.status, 0, RQR_ERR_TIMEOUT);
       return;
     }
-    if (warp == 0) {
-      // reflector of rows s.. of the winner (Sec. 3.1, sign(0) = +1)
+    if (s + 1 >= a.bsteps) break;  // the last pick needs no reflector
+    // ---- reflector of rows s.. of the winner (Sec. 3.1, sign(0) = +1) and its
+    // application to the remaining columns, in two phases, so that the scalar
+    // chain of the reflector (a square root and two divisions, slow on GB300's
+    // FP64 pipe) in the last warp overlaps the dot products in the others:
+    //   A: d_c = sum_{r >= 1} x_r y_c(r), x = the winner's rows s.. as read;
+    //   B: with v = (1, rd x_1, rd x_2, ...) and rd = 1 / (alpha - beta),
+    //      w_c = tau (y_c(0) + rd d_c), y_c(0) -= w_c, y_c(r) -= (w_c rd) x_r.
+    // Columns are spread over warps 0..PNW-2 with g threads per column (g a
+    // power of two, a group never crosses a warp), so the FP64 work of a step
+    // is spread over the SM's four sub-partitions however few columns remain.
+    const int first = max(0, s + 1 - lo);
+    const int ncol = cnt - first;
+    int g = 1;
+    while (g < 32 && ncol * (2 * g) <= (PNW - 1) * 32) g *= 2;
+    const int lg = __ffs(g) - 1;
+    const int span = ((PNW - 1) * 32) >> lg;  // columns per pass
+    const int kk = tid & (g - 1);             // this thread's place in its column's group
+    if (warp == PNW - 1) {
       T ss = T(0);
-      for (int r = lane; r < L; r += 32) {
-        const T x = v[r];
-        ss += x * x;
-      }
+      for (int r = lane; r < L; r += 32) ss += v[r] * v[r];
       ss = warp_sum(ss);
-      const T alpha = v[0];
-      T tau = T(0), rd = T(1);
-      if (L >= 2 && ss > T(0)) {
-        const T beta = -sgn0(alpha) * sqrt(ss);
-        rd = T(1) / (alpha - beta);  // one division per step: FP64 division is slow on GB300
-        tau = (beta - alpha) / beta;
-      }
-      __syncwarp();
-      for (int r = 1 + lane; r < L; r += 32) v[r] = tau == T(0) ? T(0) : v[r] * rd;
       if (lane == 0) {
-        v[0] = T(1);
+        const T alpha = v[0];
+        T tau = T(0), rd = T(1);
+        if (L >= 2 && ss > T(0)) {
+          const T beta = -sgn0(alpha) * sqrt(ss);
+          rd = T(1) / (alpha - beta);
+          tau = (beta - alpha) / beta;
+        }
         s_tau = tau;
+        s_rd = rd;
+      }
+    } else {
+      for (int base = first; base < cnt; base += span) {
+        const int pl = base + (tid >> lg);
+        T d0 = T(0), d1 = T(0);
+        if (pl < cnt) {
+          const T* y = tile + (size_t)pl * LS + s;
+          int r = 1 + kk;
+          for (; r + g < L; r += 2 * g) {
+            d0 += v[r] * y[r];
+            d1 += v[r + g] * y[r + g];
+          }
+          if (r < L) d0 += v[r] * y[r];
+        }
+        T d = d0 + d1;
+        for (int o = g >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (pl < cnt && kk == 0) dsh[pl] = d;
       }
     }
     __syncthreads();
-    if (s + 1 >= a.bsteps) break;
-    // ---- apply the reflector to the remaining columns, norms of rows s+1..
-    // One thread per column: the FP64 pipe issues a warp instruction for 32
-    // columns at once, with no shuffles or idle lanes on the short columns of
-    // the late steps. A column whose downdated norm lost too many digits gets
-    // its exact norm from the whole warp afterwards.
-    const T tau = s_tau;
+    // ---- phase B, norms of rows s+1.. (downdated: the reflector keeps the
+    // norm of rows s.., so |y(s+1:)|^2 = |y(s:)|^2 - y_s^2 with y_s updated)
+    const T tau = s_tau, rd = s_rd;
     wn = -1;
     wp = 0x7fffffff;
-    for (int base = max(0, s + 1 - lo); base < cnt; base += PT) {
-      const int pl = base + tid;
-      const bool act = pl < cnt;
-      T nn = T(-1);
-      bool redo = false;
-      if (act) {
+    if (warp < PNW - 1) {
+      for (int base = first; base < cnt; base += span) {
+        const int pl = base + (tid >> lg);
+        const bool act = pl < cnt;
         T* y = tile + (size_t)pl * LS + s;
-        T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
-        int r = 0;
-        for (; r + 4 <= L; r += 4) {
-          d0 += v[r] * y[r];
-          d1 += v[r + 1] * y[r + 1];
-          d2 += v[r + 2] * y[r + 2];
-          d3 += v[r + 3] * y[r + 3];
+        T wc = T(0), y0 = T(0);
+        if (act) {
+          y0 = y[0];
+          wc = tau * (y0 + rd * dsh[pl]);
         }
-        for (; r < L; ++r) d0 += v[r] * y[r];
-        const T dot = ((d0 + d1) + (d2 + d3)) * tau;
-        for (r = 0; r < L; ++r) y[r] -= dot * v[r];
-        const T y0 = y[0];
-        nn = nrm[pl] - y0 * y0;
-        redo = !(nn > kRecompute * ref[pl]);
-      }
-      __syncwarp();
-      unsigned m = __ballot_sync(0xffffffffu, redo);
-      while (m) {
-        // exact squared norm of rows s+1.. of the lane's column
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const int pc = base + (tid & ~31) + src;
-        const T* y = tile + (size_t)pc * LS + s;
-        T ss = T(0);
-        for (int r = 1 + lane; r < L; r += 32) ss += y[r] * y[r];
-        ss = warp_sum(ss);
-        if (lane == src) {
-          nn = ss;
-          ref[pc] = ss;
+        __syncwarp();  // every lane of the group has read y(0) before the leader writes it
+        if (act) {
+          const T wr = wc * rd;
+          for (int r = 1 + kk; r < L; r += g) y[r] -= wr * v[r];
+          if (kk == 0) {
+            y0 -= wc;
+            y[0] = y0;
+          }
         }
-      }
-      if (act) {
-        nrm[pl] = nn;
-        const long long key = norm_key(nn);
-        if (better(key, lo + pl, wn, wp)) {
-          wn = key;
-          wp = lo + pl;
+        __syncwarp();
+        T nn = T(-1);
+        bool redo = false;
+        if (act && kk == 0) {
+          nn = nrm[pl] - y0 * y0;
+          redo = !(nn > kRecompute * ref[pl]);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, redo);
+        while (m) {
+          // exact squared norm of rows s+1.. of a leader's column, by the whole warp
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const int pc = base + (((tid & ~31) + src) >> lg);
+          const T* yc = tile + (size_t)pc * LS + s;
+          T ss = T(0);
+          for (int r = 1 + lane; r < L; r += 32) ss += yc[r] * yc[r];
+          ss = warp_sum(ss);
+          if (lane == src) {
+            nn = ss;
+            ref[pc] = ss;
+          }
+        }
+        if (act && kk == 0) {
+          nrm[pl] = nn;
+          const long long key = norm_key(nn);
+          if (better(key, lo + pl, wn, wp)) {
+            wn = key;
+            wp = lo + pl;
+          }
         }
       }
     }
@@ -559,13 +589,22 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       if (e == 0 || e >= jn + 2) reduce_entry<T>(e, nc, a.part, total);
     if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status, a.wait_ns)) return false;
     const T* rb = a.rowbuf + (size_t)(jn & 1) * nc;
+    // the row entry and dot total of this thread's first column are fetched
+    // in the same round trip as thread 0's coefficient inputs
+    T rbc = T(0), totc = T(0);
+    if (tid < nc && tid > jn) {
+      rbc = __ldcg(rb + tid);
+      totc = __ldcg(total + 1 + tid);
+    }
     if (tid == 0) {
       reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
       s_rd = T(1) / s_coef[2];
     }
     __syncthreads();
     const T tau = s_coef[0], rd = s_rd;
-    for (int c = tid; c < nc; c += PT) w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) * rd) : T(0);
+    if (tid < nc) w[tid] = (tid > jn && tau != T(0)) ? tau * (rbc + totc * rd) : T(0);
+    for (int c = tid + PT; c < nc; c += PT)
+      w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) * rd) : T(0);
     __syncthreads();
     return true;
   };
@@ -610,47 +649,52 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       t1[rr] -= w1 * (i == j ? T(1) : tj[rr]);
     }
     __syncthreads();
+    // Partials of column j+1: its squared norm below the diagonal and, while
+    // reflector j is applied to columns j+2.., its dot products with them.
+    // Items c = j+1 .. nc-1 (c = j+1: the norm) are spread over the block with
+    // g threads per item (g a power of two, a group inside one warp, rows
+    // interleaved), so the FP64 work of a column step keeps all four SM
+    // sub-partitions busy however few columns remain.
     T* myp = a.part + (size_t)q * (nc + 1);
-    if (tid == PT - 1) {
-      // squared norm of column j+1 below the diagonal, in the last thread
-      // (idle in the column loop below unless nc > PT + j + 1)
-      T s0 = T(0), s1 = T(0);
-      int rr = max(lo, j + 2 - r0);
-      for (; rr + 2 <= nr; rr += 2) {
-        s0 += t1[rr] * t1[rr];
-        s1 += t1[rr + 1] * t1[rr + 1];
-      }
-      if (rr < nr) s0 += t1[rr] * t1[rr];
-      myp[0] = s0 + s1;
-    }
-    // one thread per later column: the FP64 pipe issues each warp
-    // instruction for 32 columns, with no shuffle reduction per column
-    for (int c = j + 2 + tid; c < nc; c += PT) {
-      T* x = tile + (size_t)c * RS;
-      const T wc = w[c];
-      int rr = lo;
-      if (rr < nr && r0 + rr == j) {  // row j: the reflector's implicit unit entry
-        x[rr] -= wc;
-        ++rr;
-      }
-      if (rr < nr && r0 + rr == j + 1) {  // row j+1: updated, not in the dot product
-        x[rr] -= wc * tj[rr];
-        ++rr;
-      }
+    const int nitem = nc - (j + 1);
+    int g = 1;
+    while (g < 32 && nitem * (2 * g) <= PT) g *= 2;
+    const int lg = __ffs(g) - 1;
+    const int span = PT >> lg, kk = tid & (g - 1);
+    const int rs = min(nr, max(lo, j + 2 - r0));  // first local row below column j+1's diagonal
+    for (int base = j + 1; base < nc; base += span) {
+      const int c = base + (tid >> lg);
       T acc0 = T(0), acc1 = T(0);
-      for (; rr + 2 <= nr; rr += 2) {
-        const T x0 = x[rr] - wc * tj[rr], x1 = x[rr + 1] - wc * tj[rr + 1];
-        x[rr] = x0;
-        x[rr + 1] = x1;
-        acc0 += t1[rr] * x0;
-        acc1 += t1[rr + 1] * x1;
+      if (c == j + 1) {
+        int rr = rs + kk;
+        for (; rr + g < nr; rr += 2 * g) {
+          acc0 += t1[rr] * t1[rr];
+          acc1 += t1[rr + g] * t1[rr + g];
+        }
+        if (rr < nr) acc0 += t1[rr] * t1[rr];
+      } else if (c < nc) {
+        T* x = tile + (size_t)c * RS;
+        const T wc = w[c];
+        if (kk == 0)
+          for (int rr = lo; rr < rs; ++rr)  // rows j (the reflector's unit entry) and j+1 (not in the dot product)
+            x[rr] -= r0 + rr == j ? wc : wc * tj[rr];
+        int rr = rs + kk;
+        for (; rr + g < nr; rr += 2 * g) {
+          const T x0 = x[rr] - wc * tj[rr], x1 = x[rr + g] - wc * tj[rr + g];
+          x[rr] = x0;
+          x[rr + g] = x1;
+          acc0 += t1[rr] * x0;
+          acc1 += t1[rr + g] * x1;
+        }
+        if (rr < nr) {
+          const T x0 = x[rr] - wc * tj[rr];
+          x[rr] = x0;
+          acc0 += t1[rr] * x0;
+        }
       }
-      if (rr < nr) {
-        const T x0 = x[rr] - wc * tj[rr];
-        x[rr] = x0;
-        acc0 += t1[rr] * x0;
-      }
-      myp[1 + c] = acc0 + acc1;
+      T acc = acc0 + acc1;
+      for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (c < nc && kk == 0) myp[c == j + 1 ? 0 : 1 + c] = acc;
     }
     __syncthreads();  // row j+1 of every column is final before it is published
     T* rb = a.rowbuf + (size_t)((j + 1) & 1) * nc;
@@ -712,7 +756,7 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
   C = std::max(1, std::min(sms, ceil_div(np, 8)));
   per = ceil_div(std::max(np, 1), C);
   C = ceil_div(std::max(np, 1), per);
-  return sizeof(double) * ((size_t)per * (l | 1) + l + 2 * (size_t)per);
+  return sizeof(double) * ((size_t)per * (l | 1) + l + 3 * (size_t)per);
 }
 
 // Flagged words of the pivot exchange: slots [2][C][4], candidate columns

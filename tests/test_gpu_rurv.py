@@ -13,6 +13,14 @@ g = sigma_{k1-1} - sigma_{k1}: a block's subspace moves by about u ||A|| / g
 under rounding, and through the sketch and the power step the off-diagonal
 norm by up to 1e3 u ||A||^2 / g (measured on the oracle itself: perturbing A
 by 1e-16 relative moves it by up to 7e-9 on the S-curve case, g = 2.6e-6).
+Rounding differences also compound from block to block: each block's sketch
+is taken of the trailing matrix left by the previous blocks, and on the
+Gaussian 1300 x 1280 case with q = 2 the oracle's own invariants move by a
+factor of about 4 per block under a 1e-16 relative perturbation of A (up to
+8.6e-10 ||A||_2 in the last block). Every bound is therefore also at least
+100 times the oracle's own drift under such a perturbation (fixed seed),
+measured per block: the GPU's products and panel sums round in another order,
+an effective perturbation of tens of units in the last place.
 The factorization bounds A P = Q R with Q, P orthonormal to 1e-13 are checked
 on the GPU's own outputs.
 """
@@ -57,6 +65,14 @@ def block_invariants(R, b):
     return out
 
 
+def oracle_drift(A, b, p, q, G, inv0):
+    """Per block, how far the oracle's invariants move when A is perturbed by
+    1e-16 relative (fixed seed): the conditioning of what is compared."""
+    Ap = A * (1 + 1e-16 * np.random.default_rng(0).standard_normal(A.shape))
+    inv1 = block_invariants(np.triu(oracle.rurv(Ap, b, p, q, G)[0])[:A.shape[1]], b)
+    return [(np.abs(s1 - s0).max(), abs(o1 - o0), abs(t1 - t0)) for (s1, o1, t1), (s0, o0, t0) in zip(inv1, inv0)]
+
+
 CASES = [
     # m, n, b, p, q, family
     (160, 160, 32, 0, 0, "fast"),
@@ -92,13 +108,15 @@ def test_rurv_parity(m, n, b, p, q, fam, prec):
     nA2 = sv[0]
     R0 = np.triu(F0)[:n]
     starts = inputs.block_starts(n, b)
-    for k0, (s, off, tail), (s0, off0, tail0) in zip(starts, block_invariants(R, b), block_invariants(R0, b)):
+    inv0 = block_invariants(R0, b)
+    drift = oracle_drift(A, b, p, q, G, inv0)
+    for k0, (s, off, tail), (s0, off0, tail0), (ds, doff, dtail) in zip(starts, block_invariants(R, b), inv0, drift):
         k1 = min(n, k0 + b)
         gap = sv[k1 - 1] - sv[k1] if k1 < n else nA2
-        tol = max(1e-9 * nA2, 1e3 * 2.0 ** -53 * nA2 ** 2 / max(gap, 1e-300))
-        assert np.abs(s - s0).max() <= 1e-9 * nA2
-        assert abs(off - off0) <= tol
-        assert abs(tail - tail0) <= 1e-9 * nA2
+        tol = max(1e-9 * nA2, 1e3 * 2.0 ** -53 * nA2 ** 2 / max(gap, 1e-300), 100 * doff)
+        assert np.abs(s - s0).max() <= max(1e-9 * nA2, 100 * ds), k0
+        assert abs(off - off0) <= tol, k0
+        assert abs(tail - tail0) <= max(1e-9 * nA2, 100 * dtail), k0
     # the GPU's S blocks are stored like the oracle's: strictly lower part only
     assert np.all(np.triu(WV) == 0)
 
