@@ -151,6 +151,8 @@ struct PanelBufs {
 
 template <typename T>
 size_t panel_scratch_elems(int mp, int nc, int sms);
+// flagged 8-byte words of the persistent panel's exchange (persist.cu)
+size_t panel_exchange_words(int nc, int C, size_t elem);
 
 // Unpivoted Householder QR of the mp x nc panel P (ld ldp), Sec. 3.2.
 // tau receives nc scaling factors (0 where no reflector).

@@ -484,8 +484,11 @@ template <typename T>
 size_t panel_scratch_elems(int mp, int nc, int sms) {
   int C, R;
   panel_geometry(mp, nc, sizeof(T), sms, C, R);
-  // part [C][nc+1] + rowbuf[2][nc] + coef[2][NCOEF+nc] + counter/piv (as T) + slack
-  return (size_t)C * (nc + 1) + 2 * (size_t)nc + 2 * (size_t)(NCOEF + nc) + 2 * (size_t)nc + 64;
+  // multi-launch path: part [C][nc+1] + rowbuf[2][nc] + coef[2][NCOEF+nc] + counter/piv (as T) + slack;
+  // persistent path: its flagged exchange words after 16-byte alignment
+  const size_t steps = (size_t)C * (nc + 1) + 2 * (size_t)nc + 2 * (size_t)(NCOEF + nc) + 2 * (size_t)nc + 64;
+  const size_t words = (8 * panel_exchange_words(nc, C, sizeof(T)) + 16) / sizeof(T) + 1;
+  return std::max(steps, words);
 }
 
 struct PanelScratch {};

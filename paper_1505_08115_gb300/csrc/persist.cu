@@ -5,10 +5,10 @@
 //
 // Each CTA keeps its slice resident in shared memory for all steps (sketch
 // columns of a fixed range of positions; panel rows of a fixed range), so a
-// step reads no global memory except the few values the CTAs exchange. Steps
-// are separated by an arrival barrier on a counter that only grows (one
-// device-scope atomic per CTA, no release phase), and the data exchanged
-// through global memory is reduced by every CTA (pivot winner) or by one CTA
+// step reads no global memory except the few values the CTAs exchange. The
+// values are exchanged as flagged 8-byte words (32 data bits and the step's
+// tag), so a reader waits for exactly the words it needs, with no grid
+// barrier or fence; they are reduced by every CTA (pivot winner) or by one CTA
 // per entry (panel sums) in a fixed order, so results do not depend on timing.
 // Waits are bounded by the handle's wait limit (2 s of global time unless the
 // caller sets another); a wait that runs out sets RQR_ERR_TIMEOUT in the
@@ -28,52 +28,10 @@ namespace {
 constexpr int PT = 256, PNW = PT / 32;
 constexpr double kRecompute = 1.0 / 1024.0;  // pivot norms: recompute below this fraction of the last exact one
 
-struct GridSync {
-  unsigned count;  // arrivals so far (zeroed before the launch)
-  unsigned pad0;
-  int err;         // set by a CTA whose wait ran out
-  int pad1;
-};
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Arrival barrier on a counter that only grows: CTA arrivals of step s bring
-// it to C (s + 1). Thread 0 of every CTA publishes its CTA's writes with a
-// device-scope fence and one atomic, then spins (bounded by limit_ns of global
-// time) until every CTA has arrived; false when the wait ran out or another
-// CTA gave up.
 __device__ __forceinline__ uint64_t gtime_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-__device__ bool count_barrier(unsigned* count, unsigned target, int* err, int* status, unsigned long long limit_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
-    int ok = 1;
-    if (ld_acquire(count) < target) {
-      const uint64_t t0 = gtime_ns();
-      while (ld_acquire(count) < target) {
-        if (*(volatile int*)err || gtime_ns() - t0 > limit_ns) {
-          atomicExch(err, 1);
-          atomicCAS(status, 0, RQR_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
 }
 
 // ------------------------------------------------------------ flagged words
@@ -514,117 +472,136 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
 
 // ------------------------------------------------------------ panel
 // Arguments of the persistent panel QR below: the panel, its tau, and the
-// exchange buffers (per-CTA partial sums, the published row j+1, the totals).
+// exchange words (flagged like the pivot kernel's; per step parity: every
+// CTA's partial sums, the totals, the published row).
 template <typename T>
 struct QArgs {
   int mp, nc, R;
   T* P;
   int ldp;
   T* tau;
-  T* part;    // [C][nc + 1]
-  T* rowbuf;  // [2][nc]
-  T* coef;    // [2][NCOEF + nc]
-  GridSync* gs;
+  llw* pw;  // [2][C][nc + 1] values: CTA partials (entry 0: squared norm below the diagonal, 1 + c: dot with column c)
+  llw* tw;  // [2][nc + 1] values: totals, entry e added up by CTA e mod C
+  llw* rw;  // [2][nc] values: the row of the next reflector's diagonal, from the CTA that holds it
   int* status;
-  unsigned long long wait_ns;  // limit of each arrival wait
+  unsigned long long wait_ns;  // limit of each wait for another CTA's words
 };
-
-// Column totals of the CTA partials: CTA e adds entry e of all C partial
-// vectors (one load per thread, a fixed-order tree), so every total has the
-// same value whichever CTA computes or reads it.
-template <typename T>
-__device__ __forceinline__ void reduce_entry(int e, int nc, const T* part, T* total) {
-  __shared__ T wsum[pnl::PT / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, C = gridDim.x;
-  const int nw = min(pnl::PT / 32, (C + 31) / 32);  // warps holding partials
-  T x = T(0);
-  for (int q = tid; q < C; q += pnl::PT) x += __ldcg(part + (size_t)q * (nc + 1) + e);
-  if (warp < nw) x = warp_sum(x);
-  if (lane == 0) wsum[warp] = x;
-  __syncthreads();
-  if (tid == 0) {
-    T t = T(0);
-    for (int w = 0; w < nw; ++w) t += wsum[w];
-    total[e] = t;
-  }
-  __syncthreads();
-}
 
 // Householder QR of an mp x nc panel (Sec. 3.2) as one cooperative launch:
 // each CTA keeps its rows of all nc columns in shared memory for the whole
 // panel. Per column j: the CTAs update column j+1 and the columns after it and
 // publish partial sums (squared norm of column j+1 below the diagonal, its
-// dot products with the later columns); after an arrival barrier CTA e adds
-// entry e over all CTAs; after a second barrier every CTA reads the totals and
-// computes the next reflector's coefficients itself.
+// dot products with the later columns) as flagged words; CTA e mod C waits
+// for entry e of every CTA, adds them in CTA order and publishes the total;
+// every CTA waits for the totals and the published row it needs and computes
+// the next reflector's coefficients itself. No grid barrier and no fence: each
+// word is waited for where it is used, and the totals of a step are complete
+// only after every CTA has published that step's partials, so no CTA can
+// overwrite a word of one parity while another still waits for it.
 template <typename T>
 __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
   using namespace pnl;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int WV = sizeof(T) / 4;  // flagged words per value
   const int nc = a.nc, R = a.R, C = gridDim.x;
   T* w = reinterpret_cast<T*>(smem_raw);  // [nc]
   T* tile = w + nc;                       // [nc][RS]: tile[c * RS + rr] = P(r0 + rr, c)
   __shared__ T wsum[PT / 32];
   __shared__ T s_coef[NCOEF];
   __shared__ T s_rd;  // 1 / d of the current reflector: one division per column, not one per row
+  __shared__ volatile int s_fail;  // a wait of this CTA gave up: the others stop waiting too
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // an earlier step failed: leave the panel as it is (no CTA of this launch
   // can set the word before every CTA has passed this point: the first
-  // exchange waits for all of them)
+  // exchange waits for the partials of all of them)
   if (*(volatile int*)a.status != 0) return;
+  if (tid == 0) s_fail = 0;
   const int RS = R | 1;  // odd column stride: a thread per column reads without bank conflicts
   const int r0 = q * R, r1 = min(a.mp, r0 + R), nr = max(0, r1 - r0);
-  T* total = a.coef;  // [nc + 1]
-  unsigned nbar = 0;
   for (int e = tid; e < nr * nc; e += PT) {
     const int rr = e % nr, cc = e / nr;
     tile[(size_t)cc * RS + rr] = a.P[r0 + rr + (size_t)cc * a.ldp];
   }
   __syncthreads();
-  // Exchange after the partials of column jn are published: totals, then the
-  // coefficients of jn's reflector and w[c] = tau (x_jn,c + dot_c / d), c > jn.
+  auto pword = [&](int par, int cta, int e) { return a.pw + ((size_t)(par * C + cta) * (nc + 1) + e) * WV; };
+  auto tword = [&](int par, int e) { return a.tw + ((size_t)par * (nc + 1) + e) * WV; };
+  auto rword = [&](int par, int c) { return a.rw + ((size_t)par * nc + c) * WV; };
+  auto fail = [&]() {
+    if (tid == 0) atomicCAS(a.status, 0, RQR_ERR_TIMEOUT);
+    return false;
+  };
+  // Exchange after the partials of column jn are published (tag jn + 1):
+  // totals, then the coefficients of jn's reflector and
+  // w[c] = tau (x_jn,c + dot_c / d), c > jn.
   auto exchange = [&](int jn) -> bool {
-    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status, a.wait_ns)) return false;
-    for (int e = q; e <= nc; e += C)
-      if (e == 0 || e >= jn + 2) reduce_entry<T>(e, nc, a.part, total);
-    if (!count_barrier(&a.gs->count, (unsigned)C * ++nbar, &a.gs->err, a.status, a.wait_ns)) return false;
-    const T* rb = a.rowbuf + (size_t)(jn & 1) * nc;
-    // the row entry and dot total of this thread's first column are fetched
-    // in the same round trip as thread 0's coefficient inputs
-    T rbc = T(0), totc = T(0);
-    if (tid < nc && tid > jn) {
-      rbc = __ldcg(rb + tid);
-      totc = __ldcg(total + 1 + tid);
+    const uint32_t tag = (uint32_t)jn + 1u;
+    const int par = jn & 1;
+    bool bad = false;
+    for (int e = q; e <= nc; e += C) {
+      if (!(e == 0 || e >= jn + 2)) continue;
+      T x = T(0);
+      for (int t = tid; t < C && !bad; t += PT) {
+        T v;
+        if (!ll_get<T>(pword(par, t, e), tag, v, a.wait_ns, &s_fail)) bad = true;
+        else x += v;
+      }
+      x = warp_sum(x);
+      if (lane == 0) wsum[warp] = x;
+      __syncthreads();
+      if (tid == 0 && !bad) {
+        T t = T(0);
+        for (int k = 0; k < PT / 32; ++k) t += wsum[k];
+        ll_put<T>(tword(par, e), t, tag);
+      }
+      __syncthreads();
     }
+    if (__syncthreads_or(bad)) return fail();
+    // this thread's first column's row entry and total, in the same round
+    // trip as thread 0's coefficient inputs
+    // (a panel with more columns than rows has no row jn >= mp: nobody
+    // publishes it, and its reflector is the identity, tau = 0)
+    const bool rowx = jn < a.mp;
+    T rbc = T(0), totc = T(0), alpha = T(0), below = T(0);
+    if (tid < nc && tid > jn)
+      bad = (rowx && !ll_get<T>(rword(par, tid), tag, rbc, a.wait_ns, &s_fail)) ||
+            !ll_get<T>(tword(par, 1 + tid), tag, totc, a.wait_ns, &s_fail);
+    if (tid == 0)
+      bad = (rowx && !ll_get<T>(rword(par, jn), tag, alpha, a.wait_ns, &s_fail)) ||
+            !ll_get<T>(tword(par, 0), tag, below, a.wait_ns, &s_fail);
+    if (__syncthreads_or(bad)) return fail();
     if (tid == 0) {
-      reflector_coef<T>(jn, a.mp, __ldcg(rb + jn), __ldcg(total), s_coef, q == 0 ? a.tau : nullptr, a.status);
+      reflector_coef<T>(jn, a.mp, alpha, below, s_coef, q == 0 ? a.tau : nullptr, a.status);
       s_rd = T(1) / s_coef[2];
     }
     __syncthreads();
     const T tau = s_coef[0], rd = s_rd;
     if (tid < nc) w[tid] = (tid > jn && tau != T(0)) ? tau * (rbc + totc * rd) : T(0);
-    for (int c = tid + PT; c < nc; c += PT)
-      w[c] = (c > jn && tau != T(0)) ? tau * (__ldcg(rb + c) + __ldcg(total + 1 + c) * rd) : T(0);
-    __syncthreads();
+    for (int c = tid + PT; c < nc && !bad; c += PT) {
+      T rv = T(0), tv = T(0);
+      if (c > jn && ((rowx && !ll_get<T>(rword(par, c), tag, rv, a.wait_ns, &s_fail)) ||
+                     !ll_get<T>(tword(par, 1 + c), tag, tv, a.wait_ns, &s_fail)))
+        bad = true;
+      w[c] = (c > jn && tau != T(0)) ? tau * (rv + tv * rd) : T(0);
+    }
+    if (__syncthreads_or(bad)) return fail();
     return true;
   };
   // partials of column 0 (below the diagonal) and row 0
   {
-    T* myp = a.part + (size_t)q * (nc + 1);
     T ssum = T(0);
     for (int rr = tid; rr < nr; rr += PT)
       if (r0 + rr > 0) ssum += tile[rr] * tile[rr];
     ssum = block_sum(ssum, wsum);
-    if (tid == 0) myp[0] = ssum;
+    if (tid == 0) ll_put<T>(pword(0, q, 0), ssum, 1u);
     for (int c = 1 + warp; c < nc; c += PT / 32) {
       T acc = T(0);
       for (int rr = lane; rr < nr; rr += 32)
         if (r0 + rr > 0) acc += tile[rr] * tile[(size_t)c * RS + rr];
       acc = warp_sum(acc);
-      if (lane == 0) myp[1 + c] = acc;
+      if (lane == 0) ll_put<T>(pword(0, q, 1 + c), acc, 1u);
     }
     if (r0 == 0 && nr > 0)
-      for (int c = tid; c < nc; c += PT) a.rowbuf[c] = tile[(size_t)c * RS];
+      for (int c = tid; c < nc; c += PT) ll_put<T>(rword(0, c), tile[(size_t)c * RS], 1u);
     if (!exchange(0)) return;
   }
   for (int j = 0; j < nc; ++j) {
@@ -655,7 +632,8 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
     // g threads per item (g a power of two, a group inside one warp, rows
     // interleaved), so the FP64 work of a column step keeps all four SM
     // sub-partitions busy however few columns remain.
-    T* myp = a.part + (size_t)q * (nc + 1);
+    const uint32_t ntag = (uint32_t)j + 2u;  // the tag of exchange j + 1
+    const int npar = (j + 1) & 1;
     const int nitem = nc - (j + 1);
     int g = 1;
     while (g < 32 && nitem * (2 * g) <= PT) g *= 2;
@@ -694,12 +672,11 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
       }
       T acc = acc0 + acc1;
       for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (c < nc && kk == 0) myp[c == j + 1 ? 0 : 1 + c] = acc;
+      if (c < nc && kk == 0) ll_put<T>(pword(npar, q, c == j + 1 ? 0 : 1 + c), acc, ntag);
     }
     __syncthreads();  // row j+1 of every column is final before it is published
-    T* rb = a.rowbuf + (size_t)((j + 1) & 1) * nc;
     if (j + 1 >= r0 && j + 1 < r1)
-      for (int c = j + 1 + tid; c < nc; c += PT) rb[c] = tile[(size_t)c * RS + (j + 1 - r0)];
+      for (int c = j + 1 + tid; c < nc; c += PT) ll_put<T>(rword(npar, c), tile[(size_t)c * RS + (j + 1 - r0)], ntag);
     if (!exchange(j + 1)) return;
   }
   __syncthreads();
@@ -711,9 +688,16 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
 
 }  // namespace
 
+// Flagged words of the panel exchange: partials [2][C][nc + 1], totals
+// [2][nc + 1], row [2][nc], each value in sizeof(T) / 4 words.
+size_t panel_exchange_words(int nc, int C, size_t elem) {
+  return (2 * (size_t)C * (nc + 1) + 2 * (size_t)(nc + 1) + 2 * (size_t)nc) * (elem / 4);
+}
+
 // Householder QR of the mp x nc panel as one cooperative launch; false (and
 // nothing queued) when the rows of one CTA do not fit in shared memory or the
-// grid cannot be co-scheduled. scratch: the panel scratch of panel.cu.
+// grid cannot be co-scheduled. scratch: the panel scratch of panel.cu (at
+// least panel_exchange_words(nc, C, sizeof(T)) words after 16-byte alignment).
 template <typename T>
 bool panel_qr_persist(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* scratch, int C, int R) {
   if (mp <= 0 || nc <= 0) return true;
@@ -731,13 +715,15 @@ bool panel_qr_persist(const Ctx& c, int mp, int nc, T* P, int ldp, T* tau, T* sc
     cudaGetLastError();
     return false;
   }
-  T* part = scratch;
-  T* rowbuf = part + (size_t)C * (nc + 1);
-  T* coef = rowbuf + 2 * (size_t)nc;
-  T* tail = coef + 2 * (size_t)(pnl::NCOEF + nc);
-  GridSync* gs = reinterpret_cast<GridSync*>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
-  cudaMemsetAsync(gs, 0, sizeof(GridSync), c.stream);
-  QArgs<T> a{mp, nc, R, P, ldp, tau, part, rowbuf, coef, gs, c.status, c.wait_ns};
+  // flagged exchange words, zeroed before every launch: no word carries a tag
+  // of this launch until written by it
+  llw* words = reinterpret_cast<llw*>((reinterpret_cast<uintptr_t>(scratch) + 15) & ~uintptr_t(15));
+  const size_t wv = sizeof(T) / 4;
+  llw* pw = words;
+  llw* tw = pw + 2 * (size_t)C * (nc + 1) * wv;
+  llw* rw = tw + 2 * (size_t)(nc + 1) * wv;
+  cudaMemsetAsync(words, 0, sizeof(llw) * panel_exchange_words(nc, C, sizeof(T)), c.stream);
+  QArgs<T> a{mp, nc, R, P, ldp, tau, pw, tw, rw, c.status, c.wait_ns};
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_panel_persist<T>, dim3(C), dim3(pnl::PT), args, smem, c.stream) !=
       cudaSuccess) {
