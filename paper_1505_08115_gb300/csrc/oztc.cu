@@ -65,7 +65,7 @@ constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KB
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr size_t TC_SMEM = (size_t)TC_NS * TC_STAGE_BYTES + 1024 + 256;
 
-// ------------------------------------------------------ajor, M = 128, N = n.
+// Instruction descriptor of kind::f16: bf16 x bf16 -> FP32, A and B K-major, M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
 }
