@@ -13,11 +13,32 @@ struct PanelArgs {
   int mp, nc, R, ldp;
 };
 
-// Coefficients of the reflector of column j from its squared norm below the
-// diagonal (s_below) and its diagonal entry alpha (Sec. 3.1 with sign(0)=+1).
+// tau = (beta - alpha) / beta and rd = 1 / d of a reflector, d = alpha - beta
+// (nonzero: beta has the opposite sign of alpha), with one division:
+// r = 1 / (d beta), rd = beta r, tau = -d / beta = -d^2 r (FP64 division is a
+// long dependent chain on GB300's FP64 pipe); two divisions when d beta
+// leaves the normal range.
 template <typename T>
-__device__ __forceinline__ void reflector_coef(int j, int mp, T alpha, T s_below, T* coef, T* tau_out, int* status) {
-  T tau = T(0), beta = alpha, d = T(1), has = T(0);
+__device__ __forceinline__ void tau_and_rd(T alpha, T beta, T d, T& tau, T& rd) {
+  const T db = d * beta;
+  const T tiny = sizeof(T) == 8 ? T(2.2250738585072014e-308) : T(1.1754943508222875e-38);
+  if (fabs(db) >= tiny && isfinite(db)) {
+    const T r = T(1) / db;
+    rd = beta * r;
+    tau = -(d * d) * r;
+  } else {
+    rd = T(1) / d;
+    tau = (beta - alpha) / beta;
+  }
+}
+
+// Coefficients of the reflector of column j from its squared norm below the
+// diagonal (s_below) and its diagonal entry alpha (Sec. 3.1 with sign(0)=+1);
+// rd_out (if given) receives 1 / d.
+template <typename T>
+__device__ __forceinline__ void reflector_coef(int j, int mp, T alpha, T s_below, T* coef, T* tau_out, int* status,
+                                               T* rd_out = nullptr) {
+  T tau = T(0), beta = alpha, d = T(1), has = T(0), rd = T(1);
   if (mp - j >= 2) {
     has = T(1);
     const T s = alpha * alpha + s_below;
@@ -28,7 +49,7 @@ __device__ __forceinline__ void reflector_coef(int j, int mp, T alpha, T s_below
       const T nrm = sqrt(s);
       beta = -sgn0(alpha) * nrm;
       d = alpha - beta;
-      tau = (beta - alpha) / beta;
+      tau_and_rd(alpha, beta, d, tau, rd);
     }
   }
   coef[0] = tau;
@@ -36,6 +57,7 @@ __device__ __forceinline__ void reflector_coef(int j, int mp, T alpha, T s_below
   coef[2] = d;
   coef[3] = has;
   if (tau_out) tau_out[j] = tau;
+  if (rd_out) *rd_out = rd;
 }
 
 // Last-CTA step: totals of the partials for column jn (entry 0 = squared norm

@@ -386,8 +386,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
         T tau = T(0), rd = T(1);
         if (L >= 2 && ss > T(0)) {
           const T beta = -sgn0(alpha) * sqrt(ss);
-          rd = T(1) / (alpha - beta);
-          tau = (beta - alpha) / beta;
+          pnl::tau_and_rd(alpha, beta, alpha - beta, tau, rd);
         }
         s_tau = tau;
         s_rd = rd;
@@ -570,8 +569,9 @@ __global__ void __launch_bounds__(pnl::PT) k_panel_persist(QArgs<T> a) {
             !ll_get<T>(tword(par, 0), tag, below, a.wait_ns, &s_fail);
     if (__syncthreads_or(bad)) return fail();
     if (tid == 0) {
-      reflector_coef<T>(jn, a.mp, alpha, below, s_coef, q == 0 ? a.tau : nullptr, a.status);
-      s_rd = T(1) / s_coef[2];
+      T rd1;
+      reflector_coef<T>(jn, a.mp, alpha, below, s_coef, q == 0 ? a.tau : nullptr, a.status, &rd1);
+      s_rd = rd1;
     }
     __syncthreads();
     const T tau = s_coef[0], rd = s_rd;
