@@ -86,9 +86,9 @@ int rqr_destroy(rqr_handle_t h);
 /* Rebinds the handle to another stream (cudaStream_t). */
 int rqr_set_stream(rqr_handle_t h, void* stream);
 
-/* Limit, in nanoseconds of GPU global time, of every grid-arrival wait of the
- * cooperative pivot and panel kernels (the steps that exchange values between
- * all CTAs once per column). A wait that runs out makes the call finish with
+/* Limit, in nanoseconds of GPU global time, of every wait of the cooperative
+ * pivot and panel kernels for a value another CTA publishes (the steps that
+ * exchange values between all CTAs once per column, as flagged words). A wait that runs out makes the call finish with
  * RQR_ERR_TIMEOUT in *info: every later kernel of the call sees the status
  * word and does no swap, panel or pivot work on values of the aborted step
  * (the output is then undefined, but every access stays inside the caller's

@@ -53,7 +53,7 @@ struct Ctx {
   int64_t* nlaunch;    // host-side count of kernel launches (may be null)
   KernelTimer* kt = nullptr;  // optional per-launch timing of the tcgen05 products
   int device = -1;            // CUDA device of the handle (its stream belongs to it)
-  unsigned long long wait_ns = 2000000000ull;  // limit of the grid-arrival waits of the persistent kernels
+  unsigned long long wait_ns = 2000000000ull;  // limit of the persistent kernels' waits for other CTAs' words
 };
 
 // Counts kernel launches issued through a context (tracing aid).

@@ -41,7 +41,7 @@ struct rqr_handle_s {
   cudaStream_t stream;
   int* d_status;
   int64_t nlaunch;
-  unsigned long long wait_ns;  // grid-arrival wait limit of the persistent kernels
+  unsigned long long wait_ns;  // limit of the persistent kernels' waits for other CTAs' words
   RqrProfile prof;
   rqr::KernelTimer kt;
 };

@@ -117,9 +117,10 @@ def handle(device: torch.device | None = None) -> ctypes.c_void_p:
 
 
 def set_wait_limit_ns(ns: int, device=None) -> None:
-    """Limit of the grid-arrival waits of the cooperative pivot and panel
-    kernels on this device's handle (0 restores the default of 2 s). A wait
-    that runs out ends the factorization with status 3 (timeout)."""
+    """Limit of the waits of the cooperative pivot and panel kernels for the
+    values other CTAs publish, on this device's handle (0 restores the default
+    of 2 s). A wait that runs out ends the factorization with status 3
+    (timeout)."""
     rc = load().rqr_set_wait_limit_ns(handle(device), int(ns))
     if rc != 0:
         raise RQRError(f"rqr_set_wait_limit_ns failed ({rc})")

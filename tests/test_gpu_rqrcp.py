@@ -279,11 +279,11 @@ def test_rqrcp_full_size_spike(n, b, p, emulated):
 
 
 def test_wait_limit_timeout_then_recovery():
-    """A grid-arrival wait of the cooperative pivot/panel kernels that runs out
-    ends the call with RQR_ERR_TIMEOUT (3) instead of hanging, and the handle
-    stays usable. The limit is set to 1 ns on the handle, so the first wait of
-    ordinary work for a CTA that arrives before the others gives up: no kernel
-    is altered, nothing faults. Then the default limit is restored and the same
+    """A wait of the cooperative pivot/panel kernels for another CTA's value
+    that runs out ends the call with RQR_ERR_TIMEOUT (3) instead of hanging,
+    and the handle stays usable. The limit is set to 1 ns on the handle, so the
+    first wait of ordinary work for a value not yet published gives up: no
+    kernel is altered, nothing faults. Then the default limit is restored and the same
     handle factors the same matrix correctly."""
     m, n, b, p = 1024, 1024, 64, 8
     A = inputs.a_fast(n, seed=21, m=m)
