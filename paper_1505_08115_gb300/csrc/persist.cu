@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
   T* nrm = v + l;                             // [per] squared norm of rows s.. of each column
   T* ref = nrm + a.per;                       // [per] the last exactly computed squared norm
   T* dsh = ref + a.per;                       // [per] phase-A dot products of a step
+  T* wsh = dsh + a.per;                       // [per] w_c rd of the last step for rows > s; 0 once applied
   const int LB = l + 2;                       // colbuf stride: values, norm, reference
   __shared__ long long shn[PNW];
   __shared__ int shp[PNW], shq[PNW];
@@ -254,6 +255,23 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
         bp = shp[w];
       }
     const uint32_t tag = (uint32_t)s + 1u;
+    // The last step's reflector has been applied to row s-1 of every column
+    // only (phase B); the rest of each column follows while this step's
+    // candidates travel. The two columns published now (the CTA candidate and
+    // the column at position s) get their rows s.. first.
+    const int Lp = l - s + 1;  // rows s-1.. of the last step's reflector
+    if (s > 0) {
+      const int pc = warp == 0 ? bp : warp == 1 && s != bp ? s : -1;
+      if (pc >= lo && pc < hi) {
+        T* y = tile + (size_t)(pc - lo) * LS + (s - 1);
+        const T wr = wsh[pc - lo];
+        if (wr != T(0))
+          for (int r = 1 + lane; r < Lp; r += 32) y[r] -= wr * v[r];
+        __syncwarp();
+        if (lane == 0) wsh[pc - lo] = T(0);
+      }
+      __syncthreads();
+    }
     if (tid == 0) {
       llw* sl = a.slots + ((size_t)par * C + q) * 4;
       ll_store(sl, (uint32_t)(unsigned long long)bn, tag);
@@ -270,6 +288,26 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       if (tid == 0) {
         ll_put<T>(cb + 2 * l, nrm[s - lo], tag);
         ll_put<T>(cb + 2 * (l + 1), ref[s - lo], tag);
+      }
+    }
+    // the last step's reflector on rows s.. of the remaining columns (the
+    // winner of this step overwrites v only after the waits below), g threads
+    // per column over all warps; not needed after the last pick
+    if (s > 0 && s + 1 < a.bsteps) {
+      const int firstp = max(0, s - lo);
+      const int ncolp = cnt - firstp;
+      int gp = 1;
+      while (gp < 32 && ncolp * (2 * gp) <= PT) gp *= 2;
+      const int lgp = __ffs(gp) - 1, kp = tid & (gp - 1);
+      for (int base = firstp; base < cnt; base += PT >> lgp) {
+        const int pl = base + (tid >> lgp);
+        if (pl < cnt) {
+          const T wr = wsh[pl];
+          if (wr != T(0)) {
+            T* y = tile + (size_t)pl * LS + (s - 1);
+            for (int r = 1 + kp; r < Lp; r += gp) y[r] -= wr * v[r];
+          }
+        }
       }
     }
     // ---- global winner (every CTA, identical order): thread t waits for CTA
@@ -410,44 +448,42 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
       }
     }
     __syncthreads();
-    // ---- phase B, norms of rows s+1.. (downdated: the reflector keeps the
-    // norm of rows s.., so |y(s+1:)|^2 = |y(s:)|^2 - y_s^2 with y_s updated)
+    // ---- phase B: row s of every column, and the norms of rows s+1..
+    // (downdated: the reflector keeps the norm of rows s.., so
+    // |y(s+1:)|^2 = |y(s:)|^2 - y_s^2 with y_s updated). Rows s+1.. follow at
+    // the next step's publication (w_c rd kept in wsh), except for a column
+    // whose norm is recomputed exactly: the whole warp updates it first.
     const T tau = s_tau, rd = s_rd;
     wn = -1;
     wp = 0x7fffffff;
     if (warp < PNW - 1) {
       for (int base = first; base < cnt; base += span) {
         const int pl = base + (tid >> lg);
-        const bool act = pl < cnt;
-        T* y = tile + (size_t)pl * LS + s;
-        T wc = T(0), y0 = T(0);
-        if (act) {
-          y0 = y[0];
-          wc = tau * (y0 + rd * dsh[pl]);
-        }
-        __syncwarp();  // every lane of the group has read y(0) before the leader writes it
-        if (act) {
-          const T wr = wc * rd;
-          for (int r = 1 + kk; r < L; r += g) y[r] -= wr * v[r];
-          if (kk == 0) {
-            y0 -= wc;
-            y[0] = y0;
-          }
-        }
-        __syncwarp();
+        const bool act = pl < cnt && kk == 0;
         T nn = T(-1);
         bool redo = false;
-        if (act && kk == 0) {
+        if (act) {
+          T* y = tile + (size_t)pl * LS + s;
+          T y0 = y[0];
+          const T wc = tau * (y0 + rd * dsh[pl]);
+          y0 -= wc;
+          y[0] = y0;
+          wsh[pl] = wc * rd;
           nn = nrm[pl] - y0 * y0;
           redo = !(nn > kRecompute * ref[pl]);
         }
         unsigned m = __ballot_sync(0xffffffffu, redo);
         while (m) {
-          // exact squared norm of rows s+1.. of a leader's column, by the whole warp
+          // rows s+1.. of a leader's column, then their exact squared norm, by the whole warp
           const int src = __ffs(m) - 1;
           m &= m - 1;
           const int pc = base + (((tid & ~31) + src) >> lg);
-          const T* yc = tile + (size_t)pc * LS + s;
+          T* yc = tile + (size_t)pc * LS + s;
+          __syncwarp();
+          const T wr = wsh[pc];
+          for (int r = 1 + lane; r < L; r += 32) yc[r] -= wr * v[r];
+          __syncwarp();
+          if (lane == 0) wsh[pc] = T(0);
           T ss = T(0);
           for (int r = 1 + lane; r < L; r += 32) ss += yc[r] * yc[r];
           ss = warp_sum(ss);
@@ -456,7 +492,7 @@ __global__ void __launch_bounds__(PT) k_ypick_persist(PArgs<T> a) {
             ref[pc] = ss;
           }
         }
-        if (act && kk == 0) {
+        if (act) {
           nrm[pl] = nn;
           const long long key = norm_key(nn);
           if (better(key, lo + pl, wn, wp)) {
@@ -742,7 +778,7 @@ static size_t persist_smem(int l, int np, int sms, int& C, int& per) {
   C = std::max(1, std::min(sms, ceil_div(np, 8)));
   per = ceil_div(std::max(np, 1), C);
   C = ceil_div(std::max(np, 1), per);
-  return sizeof(double) * ((size_t)per * (l | 1) + l + 3 * (size_t)per);
+  return sizeof(double) * ((size_t)per * (l | 1) + l + 4 * (size_t)per);
 }
 
 // Flagged words of the pivot exchange: slots [2][C][4], candidate columns
