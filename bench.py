@@ -56,8 +56,8 @@ def parse():
                          "products), or a mixed mode (profiling runs)")
     ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
                     help="mixed-precision modes timed on the same workload (comma list, '' for none)")
-    ap.add_argument("--c4-svd", action="store_true", help="C4: sigma_i from the FP64 SVD of A (slow)")
-    ap.add_argument("--c5-count", type=int, default=4096, help="C5: matrices in the batch")
+    ap.add_argument("--c4-svd", action="store_true", help="leg c4: sigma_i from the FP64 SVD of A (slow)")
+    ap.add_argument("--c5-count", type=int, default=4096, help="leg c5: matrices in the batch")
     ap.add_argument("--legs", default="c2,c4,c5,cpu",
                     help="further measurements: c2 (8192^2 FP64 vs FP32), c4 (URV 8192^2, q = 0, 1, 2), "
                          "c5 (4096 small FP32 matrices, batched), cpu (LAPACK dgeqp3 and the single-threaded oracle)")
@@ -231,7 +231,7 @@ def timed_calls(fn, reset, steps, stream, phases=False):
 
 
 def leg_c2(a, dev, stream):
-    """Config C2: m = n = 8192, b = 128, p = 8, N(0,1) plus a rank-200 spike
+    """Leg c2, FP64 against FP32 at 8192^2: m = n = 8192, b = 128, p = 8, N(0,1) plus a rank-200 spike
     U diag(100 0.9^i) V^T; FP64 (DMMA products) against FP32 (3xTF32 tensor-core
     products): time, residual, orthogonality, and the first block's pivots and R
     rows against the oracle (same A, same G)."""
@@ -282,7 +282,7 @@ def leg_c2(a, dev, stream):
 
 
 def leg_c4(a, dev, stream):
-    """Config C4: orthonormal-pivot URV with diagonalised blocks (Method 3,
+    """Leg c4, the URV at 8192^2: orthonormal-pivot URV with diagonalised blocks (Method 3,
     Fig. blockRRQR), m = n = 8192, b = 128, p = 10, q = 0, 1, 2, A with
     singular values 1/(1+i)^2 plus 1e-8 N(0,1) noise; FP64X and TF32 products.
     Reports GFLOP/s (URV flop model), |R_ii| / sigma_i and the off-diagonal
@@ -337,7 +337,7 @@ def leg_c4(a, dev, stream):
 
 
 def leg_c5(a, dev, stream):
-    """Config C5: 4096 FP32 matrices, rows uniform in [32, 512], cols = rows/2
+    """Leg c5, the batched form: 4096 FP32 matrices, rows uniform in [32, 512], cols = rows/2
     rounded to 8, entries N(0,1) 0.95^j. One persistent launch each for the
     batched randomized QRCP (p = 8) and the truncated URV (k = cols/4, q = 1),
     block sizes from the autotuner's cache. Reported as matrices/s and GFLOP/s
@@ -432,8 +432,8 @@ def leg_c5(a, dev, stream):
 
 def leg_cpu(a):
     """Classical CPU context: LAPACK dgeqp3 (scipy, all host cores) on a 4096^2
-    matrix of the exp(-i/800) family, and the oracle on config C1 (1000^2,
-    b = 64, p = 10) with all cores and single-threaded."""
+    matrix of the exp(-i/800) family, and the oracle on a 1000^2 matrix
+    (b = 64, p = 10) with all cores and single-threaded."""
     import json as _json
     import numpy as np
     import scipy.linalg
@@ -583,7 +583,7 @@ def main():
     A0 = make_matrix(n, a.seed + rank, dev)
     b_tuning = None
     if a.b <= 0:
-        # b from {64, 128, 192, 256} by the autotuner (cached per device model)
+        # b from {64, 128, 192, 256} by the autotuner (timed once per device model, cached)
         from paper_1505_08115_gb300 import autotune
 
         a.b, b_tuning = autotune.choose_block(A0, prec=a.prec, p=p)

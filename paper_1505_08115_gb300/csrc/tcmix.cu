@@ -5,9 +5,9 @@
 //   3xTF32 big + small TF32 planes, x ~ big + small to about 22 bits, and
 //          the three products big.big + big.small + small.big;
 //   3xBF16 hi + lo bf16 planes (about 16 bits) and hi.hi + hi.lo + lo.hi;
-// all accumulated in FP32 over the whole K range (the benchmark spec's mixed
-// precision; the paper's Sec. 2 cost model only requires the products to be
-// matrix-matrix multiplications).
+// all accumulated in FP32 over the whole K range (modes the paper does not
+// have: its Sec. 2 cost model only requires the products to be matrix-matrix
+// multiplications).
 //
 // 1. Splitting (k_mix_split_*): row r of op(A) (or of op(B)^T) becomes NP
 //    planes planes[p][r][k], K contiguous, row stride kld (a multiple of 8).

@@ -14,7 +14,7 @@ over a few hundred reflectors). URV (Method 2, p = 0): the block invariants
 of R that any orthonormal basis of the pivot subspace leaves fixed (singular
 values of each diagonal block, norms of each block row and of each trailing
 block) within 1e-4 relative, and A P = Q R, Q, P orthonormal to FP32 bounds.
-The C5 distribution itself (rows in [32, 512], decay 0.95) is checked through
+The benchmark's batch distribution itself (rows in [32, 512], decay 0.95) is checked through
 the same bounds with Gaussians drawn in the kernel.
 """
 import numpy as np
@@ -107,8 +107,8 @@ def test_batched_urv_matches_oracle(q):
             assert abs(off - off0) <= 1e-3 * nA2 and abs(tail - tail0) <= 1e-4 * nA2, i
 
 
-def test_batched_c5_distribution_generated_gaussians_and_graph_capture():
-    """The C5 shapes (rows U[32, 512], cols rows/2 rounded to 8, entries
+def test_batched_uneven_distribution_generated_gaussians_and_graph_capture():
+    """The benchmark batch's shapes (rows U[32, 512], cols rows/2 rounded to 8, entries
     N(0,1) 0.95^j), Gaussians drawn in the kernel: every factorization within
     the FP32 bounds; the launch captured in a CUDA graph and replayed gives
     the same bits (each matrix is factored by one CTA in a fixed order)."""
