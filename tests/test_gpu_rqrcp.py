@@ -278,6 +278,39 @@ def test_rqrcp_full_size_spike(n, b, p, emulated):
     assert abs(torch.linalg.norm(R).item() / torch.linalg.norm(A0).item() - 1) <= 1e-12
 
 
+def test_rqrcp_panel_multi_launch_path():
+    """A 16384 x 512 matrix with b = 256: a 16384 x 256 panel needs 166 CTAs of
+    at most 99 rows to sit in 200 KB of shared memory each, more than the 152
+    that can be co-resident, so the panel runs as one launch per column (the last CTA of
+    each launch adds up the partial sums and forms the next reflector) instead
+    of the cooperative kernel. Pivots, R and the factorization bounds as in the
+    other parity cases (probe vectors: the CPU cannot form Q at this size)."""
+    m, n, b, p = 16384, 512, 256, 8
+    A = family("fast", m, n, seed=77)
+    G = sketch_input(DOWN, 78, m, n, b, p)
+    F0, T0, perm0, _ = oracle.rqrcp(A, b, p, G, mode=DOWN)
+    Ad = dev(A)
+    T, perm, info = rqr.rqrcp_factor(Ad, b, p, G=dev(G), sketch=DOWN)
+    torch.cuda.synchronize()
+    assert info == 0
+    np.testing.assert_array_equal(perm.cpu().numpy(), perm0)
+    nA2 = np.linalg.norm(A, 2)
+    F = host(Ad)
+    assert np.abs(np.triu(F)[:n] - np.triu(F0)[:n]).max() <= 1e-12 * nA2
+    A0 = dev(A)
+    R = torch.triu(Ad)[:n]
+    g = torch.Generator(device="cuda").manual_seed(6)
+    X = torch.randn(n, 4, generator=g, device="cuda", dtype=torch.float64)
+    RX = torch.zeros(m, 4, dtype=torch.float64, device="cuda")
+    RX[:n] = R @ X
+    QRx = apply_q(Ad, T, b, RX)
+    APx = A0[:, perm.long()] @ X
+    assert (torch.linalg.norm(APx - QRx) / (nA2 * torch.linalg.norm(X))).item() <= 1e-13
+    Y = torch.randn(m, 4, generator=g, device="cuda", dtype=torch.float64)
+    QtQy = apply_q(Ad, T, b, apply_q(Ad, T, b, Y), transpose=True)
+    assert (torch.linalg.norm(QtQy - Y) / torch.linalg.norm(Y)).item() <= 1e-13
+
+
 def test_wait_limit_timeout_then_recovery():
     """A wait of the cooperative pivot/panel kernels for another CTA's value
     that runs out ends the call with RQR_ERR_TIMEOUT (3) instead of hanging,
