@@ -56,11 +56,12 @@ def parse():
                          "products), or a mixed mode (profiling runs)")
     ap.add_argument("--modes", default="tf32,3xbf16,3xtf32",
                     help="mixed-precision modes timed on the same workload (comma list, '' for none)")
-    ap.add_argument("--c4-svd", action="store_true", help="leg c4: sigma_i from the FP64 SVD of A (slow)")
-    ap.add_argument("--c5-count", type=int, default=4096, help="leg c5: matrices in the batch")
-    ap.add_argument("--legs", default="c2,c4,c5,cpu",
-                    help="further measurements: c2 (8192^2 FP64 vs FP32), c4 (URV 8192^2, q = 0, 1, 2), "
-                         "c5 (4096 small FP32 matrices, batched), cpu (LAPACK dgeqp3 and the single-threaded oracle)")
+    ap.add_argument("--urv-svd", action="store_true", help="leg urv_8192: sigma_i from the FP64 SVD of A (slow)")
+    ap.add_argument("--batch-count", type=int, default=4096, help="leg batched: matrices in the batch")
+    ap.add_argument("--legs", default="fp32_8192,urv_8192,batched,cpu",
+                    help="further measurements: fp32_8192 (8192^2 FP64 vs FP32), urv_8192 (URV 8192^2, "
+                         "q = 0, 1, 2), batched (4096 small FP32 matrices in one launch), cpu (LAPACK dgeqp3 and "
+                         "the single-threaded oracle)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the native FP64 path")
     ap.add_argument("--no-verify", action="store_true", help="skip the accuracy probe (profiling runs)")
     ap.add_argument("--seed", type=int, default=1505)
@@ -230,8 +231,8 @@ def timed_calls(fn, reset, steps, stream, phases=False):
     return tot / steps, {k: round(v["ms"] / steps, 2) for k, v in prof.items() if v["ms"] > 0}
 
 
-def leg_c2(a, dev, stream):
-    """Leg c2, FP64 against FP32 at 8192^2: m = n = 8192, b = 128, p = 8, N(0,1) plus a rank-200 spike
+def leg_fp32_8192(a, dev, stream):
+    """FP64 against FP32 at 8192^2: m = n = 8192, b = 128, p = 8, N(0,1) plus a rank-200 spike
     U diag(100 0.9^i) V^T; FP64 (DMMA products) against FP32 (3xTF32 tensor-core
     products): time, residual, orthogonality, and the first block's pivots and R
     rows against the oracle (same A, same G)."""
@@ -281,12 +282,12 @@ def leg_c2(a, dev, stream):
     return out
 
 
-def leg_c4(a, dev, stream):
-    """Leg c4, the URV at 8192^2: orthonormal-pivot URV with diagonalised blocks (Method 3,
+def leg_urv_8192(a, dev, stream):
+    """The URV at 8192^2: orthonormal-pivot URV with diagonalised blocks (Method 3,
     Fig. blockRRQR), m = n = 8192, b = 128, p = 10, q = 0, 1, 2, A with
     singular values 1/(1+i)^2 plus 1e-8 N(0,1) noise; FP64X and TF32 products.
     Reports GFLOP/s (URV flop model), |R_ii| / sigma_i and the off-diagonal
-    mass ||R - diag R||_F / ||R||_F. sigma_i: with --c4-svd the FP64 SVD of A
+    mass ||R - diag R||_F / ||R||_F. sigma_i: with --urv-svd the FP64 SVD of A
     (about 100 s on the GPU); otherwise the constructed s_i = 1/(1+i)^2 on the
     indices where Weyl's bound |sigma_i - s_i| <= ||E||_2 (E the noise,
     ||E||_2 <= 1e-8 (sqrt(m) + sqrt(n)) + small) keeps s_i within 10% of
@@ -301,7 +302,7 @@ def leg_c4(a, dev, stream):
     g = torch.Generator(device=dev).manual_seed(a.seed + 5)
     A0 = rqr.colmajor(A0 + 1e-8 * torch.randn(n, n, generator=g, device=dev, dtype=torch.float64))
     out = {"workload": f"rurv (diagonalised blocks) m=n={n} b={b} p={p}, A = U diag(1/(1+i)^2) V^T + 1e-8 N(0,1)"}
-    if a.c4_svd:
+    if a.urv_svd:
         t0 = time.perf_counter()
         sv = torch.linalg.svdvals(A0)
         torch.cuda.synchronize()
@@ -336,8 +337,8 @@ def leg_c4(a, dev, stream):
     return out
 
 
-def leg_c5(a, dev, stream):
-    """Leg c5, the batched form: 4096 FP32 matrices, rows uniform in [32, 512], cols = rows/2
+def leg_batched(a, dev, stream):
+    """The batched form: 4096 FP32 matrices, rows uniform in [32, 512], cols = rows/2
     rounded to 8, entries N(0,1) 0.95^j. One persistent launch each for the
     batched randomized QRCP (p = 8) and the truncated URV (k = cols/4, q = 1),
     block sizes from the autotuner's cache. Reported as matrices/s and GFLOP/s
@@ -351,7 +352,7 @@ def leg_c5(a, dev, stream):
     from paper_1505_08115_gb300 import autotune, inputs, rqr
     from paper_1505_08115_gb300.flops import rqrcp_flops, rurv_flops
 
-    count = a.c5_count
+    count = a.batch_count
     shapes = inputs.batch_shapes(count, seed=a.seed)
     out = {"workload": f"{count} FP32 matrices, rows U[32, 512], cols rows/2 rounded to 8, N(0,1) 0.95^j"}
     t0 = time.perf_counter()
@@ -455,7 +456,7 @@ def leg_cpu(a):
             "oracle.rqrcp(A[:200, :200], 64, 10, G[:, :200])\n"
             "t = time.perf_counter(); oracle.rqrcp(A, 64, 10, G); t = time.perf_counter() - t\n"
             "print(json.dumps({'s': t, 'gflops': rqrcp_flops(1000, 1000, 64, 10)['total'] / t / 1e9}))\n") % ROOT
-    for label, threads in (("oracle_c1_all_cores", None), ("oracle_c1_1_thread", "1")):
+    for label, threads in (("oracle_n1000_all_cores", None), ("oracle_n1000_1_thread", "1")):
         env = dict(os.environ)
         if threads:
             env["OMP_NUM_THREADS"] = threads
@@ -763,12 +764,12 @@ def main():
         out["legs"] = {}
         del A, T, work
         torch.cuda.empty_cache()
-        if "c2" in legs:
-            out["legs"]["c2"] = leg_c2(a, dev, stream)
-        if "c4" in legs:
-            out["legs"]["c4"] = leg_c4(a, dev, stream)
-        if "c5" in legs:
-            out["legs"]["c5"] = leg_c5(a, dev, stream)
+        if "fp32_8192" in legs:
+            out["legs"]["fp32_8192"] = leg_fp32_8192(a, dev, stream)
+        if "urv_8192" in legs:
+            out["legs"]["urv_8192"] = leg_urv_8192(a, dev, stream)
+        if "batched" in legs:
+            out["legs"]["batched"] = leg_batched(a, dev, stream)
         if "cpu" in legs:
             out["legs"]["cpu"] = leg_cpu(a)
 
