@@ -147,6 +147,8 @@ def _prec(dtype, emulated: bool = False, prec=None) -> int:
     overrides the default of the dtype: FP64 (FP64X with emulated=True) for
     float64 data, FP32 for float32. The mixed modes take float64 data."""
     if prec is not None:
+        if isinstance(prec, str) and prec not in PRECISIONS:
+            raise RQRError(f"unknown precision {prec!r} (one of {', '.join(PRECISIONS)})")
         code = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         if code not in PRECISIONS.values():
             raise RQRError(f"unknown precision {prec!r}")
