@@ -1,7 +1,8 @@
 """Host logic of the Python binding (no GPU): the precision codes match the C
 ABI's #defines in include/rqr.h, the status names match its RQR_ERR_* codes,
-the precision a call gets from its dtype and prec= argument, and the refusals
-(unknown names or codes, data of the wrong type)."""
+the precision a call gets from its dtype and prec= argument, the refusals
+(unknown names or codes, data of the wrong type), and the leading dimension
+passed for column-major views (padded, one row or column, empty)."""
 import os
 import re
 
@@ -51,3 +52,17 @@ def test_precision_from_dtype_and_prec():
 def test_precision_refusals(dtype, prec):
     with pytest.raises(rqr.RQRError):
         rqr._prec(dtype, prec=prec)
+
+
+def test_leading_dimension_of_column_major_views():
+    assert rqr._ld(rqr.colmajor(torch.randn(5, 3))) == 5
+    big = torch.zeros((3, 8), dtype=torch.float64).mT          # 8 x 3, ld 8
+    assert rqr._ld(big[:5, :]) == 8                             # padded leading dimension
+    assert rqr._ld(rqr.empty_colmajor(1, 4, device="cpu")) == 1
+    assert rqr._ld(torch.randn(5, 1)) == 5                      # one column: either layout is column-major
+    assert rqr._ld(rqr.empty_colmajor(0, 3, device="cpu")) == 1
+    assert rqr._ld(rqr.empty_colmajor(6, 0, device="cpu")) == 6
+    with pytest.raises(rqr.RQRError):
+        rqr._ld(torch.randn(5, 3))                              # row-major
+    with pytest.raises(rqr.RQRError):
+        rqr._ld(torch.randn(3, 8)[:, ::2])                      # strided rows
